@@ -1,0 +1,76 @@
+"""Pins of the oracle's near-equilibrium load step (Algorithm 4) and whole-run invariants."""
+import numpy as np
+import pytest
+
+from oracle import constitutive as cm
+from oracle import evolution as ev
+from oracle import phasefield as pf
+from oracle.params import AT1, AT2, CRACK_SET, DAMAGE, ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, Params
+from paper_2203_16467_gb300.inputs import eps_M, modulus_field
+
+
+def test_rescale_puts_max_driving_force_at_bound():
+    # Lines 4-10 of Algorithm 4: after scaling eps by gamma, -F_phi(x*) = (-F_phi)_max
+    # (psi_0^+ is degree-2 homogeneous).
+    rng = np.random.default_rng(3)
+    par = Params(fracture=AT1, split=SPECTRAL, ell=2.0)
+    ny = nx = 16
+    E = modulus_field(ny, nx, 4.0, 0)
+    lam, mu = cm.lame(E, par.nu)
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    phi = 0.3 * np.exp(-((x - 8.0) ** 2 + (y - 5.0) ** 2) / 8.0)      # smooth damage spot
+    eps = np.zeros((ny, nx, 2, 2)); eps[..., 1, 1] = 1.5 + 0.3 * rng.standard_normal((ny, nx))
+    eps_bar = np.array([[0.0, 0.0], [0.0, 1.5]])
+    psi = cm.psi_plus(eps, lam, mu, par.split)
+    lap = pf.laplacian(phi)
+    gamma, flag, info = ev.rescale_factor(phi, psi, eps_bar, par, False, lap)
+    assert flag and 0 < gamma < 1
+    psi2 = cm.psi_plus(gamma * eps, lam, mu, par.split)
+    mF = pf.minus_F_phi(phi, psi2, par, lap)
+    assert mF.flat[info["istar"]] == pytest.approx(par.fmax(), rel=1e-12)
+
+
+def test_no_rescale_below_threshold():
+    par = Params(fracture=AT1, split=SPECTRAL, ell=2.0)
+    phi = np.zeros((8, 8))
+    psi = np.full((8, 8), 0.05)
+    g, flag, _ = ev.rescale_factor(phi, psi, np.eye(2) * 0.1, par, False, pf.laplacian(phi))
+    assert g == 1.0 and not flag
+
+
+def test_homogeneous_run_breaks_near_elastic_limit():
+    # Homogeneous modulus: the first phase-field evolution occurs once eps_bar_yy exceeds eps_M
+    # (Sec. 3.3), and the run ends by the stiffness criterion C_bar < C_broken.
+    ell = 2.0
+    em = eps_M(1.0, 0.2, 1.0, ell)
+    par = Params(fracture=AT1, split=SPECTRAL, irreversibility=CRACK_SET, ell=ell,
+                 d_eps_bar=((0.0, 0.0), (0.0, em / 10)), mech_tol=1e-10, pf_tol=1e-10)
+    E = np.ones((16, 16))
+    # a one-pixel weak spot seeds the crack
+    E[8, 8] = 0.9
+    st, reps = ev.run(E, par, max_steps=400)
+    first = next(r for r in reps if r["dphi_L1"] > 1e-8)
+    assert first["eps_bar"][1, 1] >= 0.85 * em
+    assert first["eps_bar"][1, 1] <= 1.1 * em
+    assert reps[-1]["broken"]
+
+
+@pytest.mark.parametrize("split,fracture,irr", [(SPECTRAL, AT1, CRACK_SET), (ISOTROPIC, AT2, DAMAGE),
+                                                (SPECTRAL_STRESSFREE, AT1, DAMAGE)])
+def test_short_run_invariants(split, fracture, irr):
+    ell = 2.0
+    em = eps_M(1.0, 0.2, 1.0, ell)
+    par = Params(fracture=fracture, split=split, irreversibility=irr, ell=ell,
+                 d_eps_bar=((0.0, 0.0), (0.0, em / 8)), mech_tol=1e-8, pf_tol=1e-8)
+    E = modulus_field(24, 24, 4.0, 7)
+    st = ev.State.initial(E)
+    for _ in range(60):
+        phi_old = st.phi.copy()
+        rep = ev.load_step(st, par)
+        assert np.all(st.phi >= pf.phi_con(phi_old, par) - 1e-12)    # Eq. irreversibility
+        assert st.phi.min() >= -1e-12
+        assert st.phi.max() <= 1.0 + 1e-6
+        if rep["rescaled"]:
+            assert rep["gamma"] < 1.0
+        if rep["broken"]:
+            break
