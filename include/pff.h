@@ -1,0 +1,243 @@
+/*
+ * pff.h -- C ABI of libpff, a GB300 (sm_103a) implementation of the staggered
+ * per-load-step solve of quasi-static phase-field fracture of
+ * W. B. Andrews and L. Pastewka, "Crack-path selection in phase-field models
+ * for brittle fracture", arXiv:2203.16467.
+ *
+ * One problem = one periodic 2-D pixel grid (nx columns along x, ny rows along
+ * y, pixel size dx) with a heterogeneous Young's modulus E(x), a uniform
+ * Poisson ratio, a phase field phi (the paper's crack field) and a strain
+ * eps = eps_bar + eps* (Sec. 3.1.1: the strain, not the displacement, is the
+ * unknown).  A load step is one pass of the while-loop of Algorithm 4
+ * (near-equilibrium evolution, Sec. 3.2.3):
+ *   mechanics (Fourier-Galerkin Newton-CG, Sec. 3.1.1)
+ *   -> rescale of eps when -F_phi exceeds its bound (Algorithm 4 lines 4-10)
+ *   -> phase field (BCCG, Algorithm 1, Sec. 3.1.2)
+ *   -> stiffness C-bar and strain increment (Algorithm 4 lines 12-14).
+ *
+ * Conventions shared by every entry point:
+ *   - Fields are row-major with y the slow index: value (y, x) at y*nx + x.
+ *   - Tensor fields (strain, stress) are 3 planes of nx*ny values in the order
+ *     xx, yy, xy (tensor shear component, not engineering shear).
+ *   - Host arrays are FP64 regardless of the problem's storage precision and
+ *     are owned by the caller; the library copies in/out and keeps no pointer.
+ *   - on_device != 0 means the pointer is a CUDA device pointer on the
+ *     problem's device (FP64, same layout); the copy runs on the problem's stream.
+ *   - The library owns all device memory of a problem; it is freed by
+ *     pff_destroy_problem.  Device pointers returned by pff_get_device_ptr
+ *     stay valid until then.
+ *   - Every function returns PFF_OK (0) or a negative PFF_ERR_* code; no
+ *     exception crosses the ABI.  pff_last_error(h) returns a message owned
+ *     by the handle (valid until the next call on it).  A handle is not
+ *     thread-safe; different handles may be used from different threads.
+ *   - Grid sizes: nx and ny are powers of two from 16 to 2048.
+ *   - The library needs an sm_103a GPU; there is no CPU fallback.
+ */
+#ifndef PFF_H
+#define PFF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PFF_OK = 0,
+    PFF_ERR_INVALID_ARG = -1,
+    PFF_ERR_OOM = -2,
+    PFF_ERR_NOT_CONVERGED = -3,
+    PFF_ERR_BARRIER_TIMEOUT = -4,
+    PFF_ERR_CUDA = -5,
+    PFF_ERR_STATE = -6
+};
+
+/* Storage / arithmetic precision of a problem. */
+enum {
+    PFF_FP64 = 0,   /* all fields and arithmetic in FP64 */
+    PFF_MIXED = 1   /* fields and pointwise/FFT arithmetic in FP32; dot products,
+                       norms, scalars, the driving-force maximum and the
+                       phase-field bound decisions in FP64 */
+};
+
+/* Local fracture energy f(phi) (Eq. fracturelocal): AT1 f = phi, c_w = 8/3;
+ * AT2 f = phi^2, c_w = 2 (the form whose optimal profile is Eq. AT2_analytical). */
+enum { PFF_AT1 = 1, PFF_AT2 = 2 };
+
+/* Energy split (Sec. 2.1).  SPECTRAL_STRESSFREE is the non-variational pairing
+ * of the strain-spectral crack driving force with the isotropic (stress-free
+ * crack) contact model. */
+enum { PFF_ISOTROPIC = 0, PFF_SPECTRAL = 1, PFF_SPECTRAL_STRESSFREE = 2 };
+
+/* Irreversibility (Eq. constraint_field): within the crack set phi >= 0.9, or
+ * in the whole domain ("damage"). */
+enum { PFF_CRACK_SET = 0, PFF_DAMAGE = 1 };
+
+/* Field selectors for pff_get_fields / pff_get_device_ptr. */
+enum {
+    PFF_FIELD_STRAIN = 0,         /* eps = eps_bar + eps*, 3 planes */
+    PFF_FIELD_EPS_STAR = 1,       /* eps*, 3 planes */
+    PFF_FIELD_STRESS = 2,         /* sigma(eps, phi) of the contact model, 3 planes */
+    PFF_FIELD_PHI = 3,            /* phi */
+    PFF_FIELD_PSI_PLUS = 4,       /* psi_0^+(eps) of the crack-driving-force model */
+    PFF_FIELD_DRIVING_FORCE = 5,  /* -F_phi(phi, eps) */
+    PFF_FIELD_MODULUS = 6,        /* E */
+    PFF_FIELD_ACTIVE = 7,         /* 1.0 where the last BCCG iterate had v = v_con and r > 0, else 0.0 */
+    PFF_FIELD_UPDATE = 8          /* v = phi_new - phi_old of the last phase-field solve */
+};
+
+/* Model and solver parameters (Sec. 3.3).  pff_default_params fills the
+ * paper's values: nu 0.2, G_c 1, ell 1, dx 1, tolerances 1e-6,
+ * (dphi)_min 1e-3, (-F_phi)_max 0.7 G_c/ell, (-h' psi_0^+)_thresh 1 G_c/ell,
+ * eta/dt = 2^-16 G_c/ell ((dt)_max = 2^16 eta/(G_c/ell)), C_broken <= 0 meaning
+ * 0.01 * mean(E). */
+typedef struct pff_params {
+    double nu;                 /* Poisson ratio (plane strain Lame constants) */
+    double Gc;                 /* critical energy release rate */
+    double ell;                /* crack width parameter */
+    double dx;                 /* pixel size */
+    double mech_tol;           /* Newton stop: ||P sigma||_2 <= mech_tol * ||C_0 : eps_bar||_2 */
+    double mech_cg_rtol;       /* inner CG relative tolerance of nonlinear (spectral-stress) Newton steps */
+    int mech_max_newton;
+    int mech_max_cg;
+    double pf_tol;             /* BCCG stop: ||r||_2 <= max(pf_tol ||r^0||_2, pf_atol) */
+    double pf_atol;
+    int pf_max_iter;
+    double eta_over_dt;        /* eta / dt of the backward-Euler phase-field step; < 0: default */
+    double F_max;              /* (-F_phi)_max; < 0: default */
+    double thresh;             /* (-h' psi_0^+)_thresh; < 0: default */
+    double dphi_min;           /* (dphi)_min, with ||dphi||_1 = (dx/ell)^2 sum |dphi| */
+    double C_broken;           /* termination stiffness; <= 0: 0.01 * mean(E) */
+    double crack_set_threshold;/* 0.9 in Eq. constraint_field */
+    double d_eps_bar[3];       /* strain increment (xx, yy, xy) */
+    int compute_energies;      /* fill F_e and F_f in step reports (one extra scalar FFT pair per step) */
+} pff_params;
+
+/* Per-load-step report.  eps_bar is the macroscopic strain the step ended
+ * with before the increment (after any rescale); sig_bar is the mean stress
+ * sigma(eps_n, phi_{n+1}) (Algorithm 4 line 12). */
+typedef struct pff_step_report {
+    double eps_bar[3];
+    double sig_bar[3];
+    double C_bar;
+    double gamma;              /* rescale factor (1.0 when no rescale) */
+    double dphi_L1;
+    double F_e;                /* elastic energy sum psi dA of the contact model */
+    double F_f;                /* fracture energy of Eq. Ff */
+    double mF_max;             /* max of -F_phi before the rescale */
+    double D_max;              /* max of -h' psi_0^+ before the rescale */
+    double mech_res;           /* final ||P sigma||_2 */
+    double pf_res;             /* final ||r||_2 of BCCG */
+    int rescaled;
+    int incremented;
+    int newton_iters;
+    int mech_cg_iters;
+    int bccg_iters;
+    int n_active;
+    int istar;                 /* linear index of argmax -F_phi */
+    int broken;                /* C_bar < C_broken */
+    int status;                /* PFF_OK or PFF_ERR_NOT_CONVERGED */
+} pff_step_report;
+
+typedef struct pff_problem pff_problem;
+typedef struct pff_batch pff_batch;
+
+/* Fill *p with the paper's default parameters (Sec. 3.3). */
+int pff_default_params(pff_params* p);
+
+/* Create a problem of nx x ny pixels on the current CUDA device.
+ * precision: PFF_FP64 or PFF_MIXED.  cuda_stream: a cudaStream_t (may be NULL
+ * for the legacy default stream) on which every kernel and copy of this
+ * problem is issued.  Initial state: E = 1, phi = 0, eps = 0, default params,
+ * model AT1 / SPECTRAL / CRACK_SET.  PFF_ERR_OOM if device memory runs out. */
+int pff_create_problem(int nx, int ny, int precision, void* cuda_stream, pff_problem** out);
+int pff_destroy_problem(pff_problem* h);
+const char* pff_last_error(pff_problem* h);
+/* Grid size and precision of a problem. */
+int pff_problem_info(pff_problem* h, int* nx, int* ny, int* precision);
+/* Device bytes held by a problem of this size and precision (for admission). */
+size_t pff_problem_bytes(int nx, int ny, int precision);
+
+int pff_set_params(pff_problem* h, const pff_params* p);
+int pff_get_params(pff_problem* h, pff_params* p);
+/* fracture: PFF_AT1|PFF_AT2; split: PFF_ISOTROPIC|PFF_SPECTRAL|PFF_SPECTRAL_STRESSFREE;
+ * irreversibility: PFF_CRACK_SET|PFF_DAMAGE (Sec. 2.1, Eq. constraint_field). */
+int pff_set_model(pff_problem* h, int fracture, int split, int irreversibility);
+/* Young's modulus field E(x) > 0, nx*ny values. */
+int pff_set_modulus_field(pff_problem* h, const double* E, int on_device);
+/* Phase field, nx*ny values in [0, 1] (initial condition; default 0). */
+int pff_set_phase_field(pff_problem* h, const double* phi, int on_device);
+/* Strain state: eps_star (3 planes, may be NULL for zero) and eps_bar[3] (host). */
+int pff_set_strain(pff_problem* h, const double* eps_star, const double eps_bar[3], int on_device);
+/* Reset the near-equilibrium Flag of Algorithm 4 (set once the trigger is met). */
+int pff_set_flag(pff_problem* h, int flag);
+
+/* Run n_steps load steps (Algorithm 4 iterations); out (n_steps entries, may
+ * be NULL) receives a report per step.  Stops early, returning the number of
+ * steps done through *steps_done (may be NULL), once C_bar < C_broken.
+ * Returns PFF_ERR_NOT_CONVERGED if a sub-solver hit its iteration cap (the
+ * state is kept). */
+int pff_step_load(pff_problem* h, int n_steps, pff_step_report* out, int* steps_done);
+
+/* Single sub-problems on the current state (for parity checks of one solve):
+ * the mechanics Newton-CG solve at the current eps_bar and phi (Sec. 3.1.1);
+ * and the phase-field BCCG solve with the current strain and phi_con(phi)
+ * (Sec. 3.1.2, Algorithm 1), which replaces phi by phi + v. */
+int pff_solve_mechanics(pff_problem* h, pff_step_report* out);
+int pff_solve_phase_field(pff_problem* h, pff_step_report* out);
+
+/* Copy a field out (FP64, host).  Tensor fields fill 3*nx*ny values. */
+int pff_get_fields(pff_problem* h, int which, double* host_out);
+/* Device view of a stored field: *p receives the device pointer, *dtype 0 for
+ * FP64 / 1 for FP32; tensor fields are 3 contiguous planes.  Only fields that
+ * are stored (EPS_STAR, PHI, MODULUS) are available. */
+int pff_get_device_ptr(pff_problem* h, int which, void** p, int* dtype);
+
+/* Operator entry points on one problem's grid (single rows of the path):
+ * pff_apply_projection: out = F^-1 Gamma F in, the compatibility projection of
+ *   Sec. 3.1.1 applied to a 3-plane tensor field (Nyquist modes of Gamma are 0).
+ * pff_apply_laplacian: out = nabla^2_N in (Sec. 3.1.2).
+ * pff_constitutive: for strain eps (3 planes) and phi, returns the stress
+ *   (3 planes), psi_0^+ (1 plane) and, if p3 != NULL, the tangent C:p (3 planes)
+ *   of the problem's model (Sec. 2.1, Sec. 3.1.1); any output may be NULL.
+ * All arrays are FP64 host arrays; the arithmetic runs in the problem's precision. */
+int pff_apply_projection(pff_problem* h, const double* in3, double* out3);
+int pff_apply_laplacian(pff_problem* h, const double* in, double* out);
+int pff_constitutive(pff_problem* h, const double* eps3, const double* phi, const double* p3,
+                     double* sig3, double* psi, double* tang3);
+
+/* Batching: several problems (any sizes, precisions, models) advanced
+ * together.  pff_batch_admit fails with PFF_ERR_OOM if the problem's device
+ * bytes do not fit the remaining budget or PFF_ERR_STATE if all slots are
+ * taken.  pff_batch_step runs n_steps load steps of every admitted, not yet
+ * broken problem; problems of equal size and precision share every kernel
+ * launch.  reports: max_slots * n_steps entries, slot-major (may be NULL);
+ * steps_done: max_slots entries (may be NULL). */
+int pff_create_batch(int max_slots, size_t hbm_budget, void* cuda_stream, pff_batch** out);
+int pff_destroy_batch(pff_batch* b);
+int pff_batch_admit(pff_batch* b, pff_problem* h, int* slot);
+int pff_batch_release(pff_batch* b, int slot);
+int pff_batch_step(pff_batch* b, int n_steps, pff_step_report* reports, int* steps_done);
+
+/* Library-wide counters: kernel launches issued since load (for benchmarks). */
+unsigned long long pff_kernel_launches(void);
+
+/* Kernel timing for benchmarks.  When enabled, every launch of the library is
+ * bracketed by CUDA events on its own stream; pff_timing_read returns the
+ * summed device time (ms) and the launch count of one kernel class since the
+ * last reset.  family: 0 row-forward (FFT along x with a fused prologue),
+ * 1 row-inverse (inverse FFT along x with a fused epilogue), 2 column pass,
+ * 3 elementwise; op: the step within the family, in load-step order
+ * (row-forward: 0 Newton residual, 1 mechanics CG, 2 phi, 3 BCCG direction,
+ * 4 BCCG iterate; row-inverse: 0 Newton, 1 CG, 2 Laplacian, 3 energy,
+ * 4 BCCG direction, 5 BCCG residual; column: 0 Newton, 1 CG, 3 driving force,
+ * 4 BCCG; elementwise: 0 fold, 1 BCCG start, 2 post-step, 3 driving-force
+ * maximum).  Enabling, resetting and reading synchronize the device. */
+int pff_timing_enable(int on);
+int pff_timing_reset(void);
+int pff_timing_read(int family, int op, double* total_ms, unsigned long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFF_H */

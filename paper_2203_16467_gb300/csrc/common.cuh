@@ -1,0 +1,325 @@
+// common.cuh -- device data layout, per-problem control block, pointwise
+// constitutive model (Sec. 2.1) and deterministic reductions shared by every
+// kernel of libpff.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pff {
+
+// ---------------------------------------------------------------------------
+// complex helpers
+template <typename T> struct CT;
+template <> struct CT<float> { using t = float2; };
+template <> struct CT<double> { using t = double2; };
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) { return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) { return C{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y}; }
+
+// model enums (mirror include/pff.h)
+enum { AT1 = 1, AT2 = 2 };
+enum { ISOTROPIC = 0, SPECTRAL = 1, SPECTRAL_STRESSFREE = 2 };
+enum { CRACK_SET = 0, DAMAGE = 1 };
+
+// ---------------------------------------------------------------------------
+// Control block of one problem (device memory).  Scalars of the iterative
+// solvers live here so that kernels chain without host round trips.  Flags
+// come in pairs (x_a, x_b): a kernel never writes a flag that kernels of the
+// same launch read, so early-exit decisions are consistent across its blocks.
+struct Ctrl {
+    // macroscopic strain and loading
+    double eps_bar[3];
+    double sumE2;           // sum of E^2 over pixels (scale of the mechanics tolerance)
+    double sumE;            // sum of E
+    // mechanics
+    double mech_target, R2, rr, pAp, rAp, qq, alpha, beta, cg_target;
+    int nd_a, nd_b, newton_it, needs_fold;
+    int cg_a, cg_b, cg_it, cg_total, cg_break;
+    // near-equilibrium rescale (Algorithm 4 lines 4-10)
+    double mF_max, D_max, Rf_star, D_star, gamma;
+    int istar, flag, rescaled;
+    // phase field (Algorithm 1)
+    double pf_rr, pf_rp, pJp, pf_alpha, pf_beta, pf_target;
+    int pf_a, pf_b, pf_it, pf_break, n_active;
+    // post-step (Algorithm 4 lines 12-14)
+    double rep_eps_bar[3], sig_bar[3], C_bar, dphi, Fe, Ff;
+    int incremented, broken;
+    int status;             // bit0: mechanics cap hit, bit1: BCCG cap hit
+    unsigned counter;       // last-block reduction counter (reset by the last block)
+    int pad;
+};
+
+// Model constants of a problem, resolved on the host.
+struct Consts {
+    double lam_c, mu_c;     // lambda = lam_c * E, mu = mu_c * E (plane strain)
+    double c;               // G_c / (c_w ell)
+    double kappa;           // 2 c ell^2 (coefficient of -nabla^2 in J)
+    double ell2;            // ell^2
+    double eta_dt;          // eta / dt
+    double cf2;             // c * f''
+    double Fmax, thresh, dphi_min, C_broken, crack_thr;
+    double mech_tol, mech_cg_rtol, pf_tol, pf_atol, pf_floor;
+    double d_eps_bar[3];
+    double dA;              // pixel area
+    double inv_n;           // 1 / (nx ny)
+    double L1_scale;        // (dx/ell)^2
+    double two_pi_over_Lx, two_pi_over_Ly;
+    int max_newton, max_cg, max_pf;
+    int fracture, split, irrev;
+};
+
+// Device descriptor of one problem's fields (all arrays nx*ny, row-major).
+// Phase-field work vectors alias the mechanics CG vectors:
+//   v = th[0], rb = th[1], pb = th[2], a = r[0], b = r[1], vcon = r[2].
+template <typename T>
+struct Desc {
+    using C = typename CT<T>::t;
+    T* E;
+    T* phi;
+    T* eps[3];
+    T* th[3];
+    T* r[3];
+    T* p[3];
+    T* q[3];
+    T* lap;
+    T* aux;
+    uint8_t* flags;
+    C* S;                   // spectral buffer [3][ny][wp]
+    const C* tw;            // twiddle tables of this device
+    double* part;           // reduction partials [blocks * 8]
+    Ctrl* ctrl;
+    int nx, ny, wp, pad;
+    Consts k;
+};
+
+// ---------------------------------------------------------------------------
+// flag access (bypass L1: flags are written by other kernels / blocks)
+__device__ __forceinline__ int ldflag(const int* p) { return __ldcg(p); }
+__device__ __forceinline__ double ldd(const double* p) { return __ldcg(p); }
+
+// ---------------------------------------------------------------------------
+// Per-thread accumulation.  FP64 problems accumulate in double.  FP32 problems
+// accumulate products exactly split (fmaf) and summed with Knuth's two-sum in
+// a float pair, and switch to double at the warp level: the pointwise work
+// stays on the FP32 pipe while the sums keep FP64-level accuracy.
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ void addp(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        float t = s + x;
+        float z = t - s;
+        c += (s - (t - z)) + (x - z);
+        s = t;
+    }
+    __device__ __forceinline__ void addp(float a, float b) {
+        float pr = a * b;
+        float e = fmaf(a, b, -pr);
+        add(pr);
+        c += e;
+    }
+    __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+};
+
+// Block reduction of NR doubles into part[blockIdx.x*NR + k]; the last block
+// of the problem (by an atomic ticket) sums all partials in a fixed order and
+// returns true with the totals in tot (valid in thread 0).  Deterministic: the
+// summation tree depends only on the grid shape.
+template <int NR, int NT>
+__device__ __forceinline__ bool reduce_last(double (&v)[NR], double* part, unsigned* counter, int nblocks,
+                                            double (&tot)[NR]) {
+    __shared__ double sh[NR][NT / 32];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[k][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            double x = 0.0;
+            for (int w = 0; w < NT / 32; ++w) x += sh[k][w];
+            __stcg(&part[(size_t)blockIdx.x * NR + k], x);
+        }
+        __threadfence();
+        unsigned t = atomicAdd(counter, 1u);
+        s_last = (t == (unsigned)(nblocks - 1));
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    // fixed-order sum of the partials: thread t takes blocks t, t+NT, ... in order
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        double x = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += NT) x += __ldcg(&part[(size_t)b * NR + k]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[k][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            double x = 0.0;
+            for (int w = 0; w < NT / 32; ++w) x += sh[k][w];
+            tot[k] = x;
+        }
+        *counter = 0u;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise constitutive model (Sec. 2.1).  Strain / stress as (xx, yy, xy)
+// with xy the tensor shear component.  Lame constants for plane strain.
+template <typename T> __device__ __forceinline__ T rp(T x) { return x > T(0) ? x : T(0); }
+template <typename T> __device__ __forceinline__ T rm(T x) { return x < T(0) ? x : T(0); }
+template <typename T> __device__ __forceinline__ T hv(T x) { return x > T(0) ? T(1) : T(0); }
+
+// Principal strains e1 >= e2 and the eigen-projector frame of a symmetric
+// 2x2 tensor without explicit eigenvectors: with d = (xx-yy)/2, rad =
+// sqrt(d^2 + xy^2), u = d/rad, w = xy/rad:
+//   P1 = 1/2 [[1+u, w], [w, 1-u]],  P2 = I - P1,  S = [[-w, u], [u, w]]
+// (S = n1 n2^T + n2 n1^T).  deg marks coincident principal strains.
+template <typename T>
+struct Eig2 {
+    T e1, e2, u, w, tr;
+    bool deg;
+    __device__ __forceinline__ Eig2(T xx, T yy, T xy) {
+        tr = xx + yy;
+        T d = T(0.5) * (xx - yy);
+        T rad = sqrt(d * d + xy * xy);
+        e1 = T(0.5) * tr + rad;
+        e2 = T(0.5) * tr - rad;
+        T scale = fmax(fabs(e1), fabs(e2));
+        deg = !(T(2) * rad > T(1e-12) * scale) || rad == T(0);
+        if (deg) { u = T(1); w = T(0); }
+        else { T inv = T(1) / rad; u = d * inv; w = xy * inv; }
+    }
+};
+
+// sigma_0^+ (sp) and sigma_0^- (sm) of the strain-spectral split
+// (Eq. stress_spectral) and psi_0^+ (Eq. strain_spectral_en).
+template <typename T>
+__device__ __forceinline__ void spectral_split(T xx, T yy, T xy, T lam, T mu, T* sp, T* sm, T& psip) {
+    Eig2<T> g(xx, yy, xy);
+    T a1 = rp(g.e1), a2 = rp(g.e2), b1 = rm(g.e1), b2 = rm(g.e2);
+    T trp = rp(g.tr), trm = rm(g.tr);
+    // eps^+ = a1 P1 + a2 P2
+    T hs = T(0.5) * (a1 + a2), hd = T(0.5) * (a1 - a2);
+    T epxx = hs + hd * g.u, epyy = hs - hd * g.u, epxy = hd * g.w;
+    T ms = T(0.5) * (b1 + b2), md = T(0.5) * (b1 - b2);
+    T emxx = ms + md * g.u, emyy = ms - md * g.u, emxy = md * g.w;
+    sp[0] = lam * trp + T(2) * mu * epxx;
+    sp[1] = lam * trp + T(2) * mu * epyy;
+    sp[2] = T(2) * mu * epxy;
+    sm[0] = lam * trm + T(2) * mu * emxx;
+    sm[1] = lam * trm + T(2) * mu * emyy;
+    sm[2] = T(2) * mu * emxy;
+    psip = T(0.5) * lam * trp * trp + mu * (a1 * a1 + a2 * a2);
+}
+
+template <typename T>
+__device__ __forceinline__ T psi_iso(T xx, T yy, T xy, T lam, T mu) {
+    T tr = xx + yy;
+    return T(0.5) * lam * tr * tr + mu * (xx * xx + yy * yy + T(2) * xy * xy);
+}
+
+template <typename T>
+__device__ __forceinline__ T psi_spectral(T xx, T yy, T xy, T lam, T mu) {
+    Eig2<T> g(xx, yy, xy);
+    T a1 = rp(g.e1), a2 = rp(g.e2), trp = rp(g.tr);
+    return T(0.5) * lam * trp * trp + mu * (a1 * a1 + a2 * a2);
+}
+
+// psi_0^+ of the crack-driving-force model (spectral for SPECTRAL and SPECTRAL_STRESSFREE).
+template <typename T>
+__device__ __forceinline__ T psi_plus(int split, T xx, T yy, T xy, T lam, T mu) {
+    return split == ISOTROPIC ? psi_iso(xx, yy, xy, lam, mu) : psi_spectral(xx, yy, xy, lam, mu);
+}
+
+// Stress of the contact model: isotropic for ISOTROPIC and SPECTRAL_STRESSFREE.
+template <typename T>
+__device__ __forceinline__ void stress(int split, T xx, T yy, T xy, T hphi, T lam, T mu, T* s) {
+    if (split == SPECTRAL) {
+        T sp[3], sm[3], psip;
+        spectral_split(xx, yy, xy, lam, mu, sp, sm, psip);
+        s[0] = hphi * sp[0] + sm[0];
+        s[1] = hphi * sp[1] + sm[1];
+        s[2] = hphi * sp[2] + sm[2];
+    } else {
+        T tr = xx + yy;
+        s[0] = hphi * (lam * tr + T(2) * mu * xx);
+        s[1] = hphi * (lam * tr + T(2) * mu * yy);
+        s[2] = hphi * (T(2) * mu * xy);
+    }
+}
+
+// Energy density psi = h psi_0^+ + psi_0^- of the contact model (Eq. psi_schema).
+template <typename T>
+__device__ __forceinline__ T energy(int split, T xx, T yy, T xy, T hphi, T lam, T mu) {
+    if (split == SPECTRAL) {
+        Eig2<T> g(xx, yy, xy);
+        T a1 = rp(g.e1), a2 = rp(g.e2), b1 = rm(g.e1), b2 = rm(g.e2);
+        T trp = rp(g.tr), trm = rm(g.tr);
+        T pp = T(0.5) * lam * trp * trp + mu * (a1 * a1 + a2 * a2);
+        T pm = T(0.5) * lam * trm * trm + mu * (b1 * b1 + b2 * b2);
+        return hphi * pp + pm;
+    }
+    return hphi * psi_iso(xx, yy, xy, lam, mu);
+}
+
+// Tangent C:p of the contact model at strain eps (Sec. 3.1.1).  Spectral:
+// Daleckii-Krein derivative of eps -> eps^+ in the frame (P1, P2, S):
+//   D+[p] = H(e1)(P1:p)P1 + H(e2)(P2:p)P2 + g12 (S:p/2) S,
+//   g12 = (<e1>_+ - <e2>_+)/(e1 - e2)  (H(e1) for coincident e1 = e2),
+// sigma' = h (lam H(tr) tr p I + 2 mu D+) + lam (1 - H(tr)) tr p I + 2 mu (p - D+).
+template <typename T>
+__device__ __forceinline__ void tangent(int split, T xx, T yy, T xy, T hphi, T lam, T mu,
+                                        T pxx, T pyy, T pxy, T* out) {
+    T trp = pxx + pyy;
+    if (split == SPECTRAL) {
+        Eig2<T> g(xx, yy, xy);
+        T dxx, dyy, dxy;
+        if (g.deg) {
+            T H = hv(g.e1);
+            dxx = H * pxx; dyy = H * pyy; dxy = H * pxy;
+        } else {
+            T H1 = hv(g.e1), H2 = hv(g.e2);
+            T g12 = (rp(g.e1) - rp(g.e2)) / (g.e1 - g.e2);
+            T u = g.u, w = g.w;
+            T P1p = T(0.5) * ((T(1) + u) * pxx + (T(1) - u) * pyy + T(2) * w * pxy);
+            T P2p = T(0.5) * ((T(1) - u) * pxx + (T(1) + u) * pyy - T(2) * w * pxy);
+            T Sp = T(0.5) * (-w * pxx + w * pyy + T(2) * u * pxy);
+            T c1 = H1 * P1p, c2 = H2 * P2p, c3 = g12 * Sp;
+            dxx = T(0.5) * (c1 * (T(1) + u) + c2 * (T(1) - u)) - c3 * w;
+            dyy = T(0.5) * (c1 * (T(1) - u) + c2 * (T(1) + u)) + c3 * w;
+            dxy = T(0.5) * (c1 * w - c2 * w) + c3 * u;
+        }
+        T Ht = hv(g.tr);
+        T lp = lam * Ht * trp, lm = lam * (T(1) - Ht) * trp;
+        out[0] = hphi * (lp + T(2) * mu * dxx) + lm + T(2) * mu * (pxx - dxx);
+        out[1] = hphi * (lp + T(2) * mu * dyy) + lm + T(2) * mu * (pyy - dyy);
+        out[2] = hphi * (T(2) * mu * dxy) + T(2) * mu * (pxy - dxy);
+    } else {
+        out[0] = hphi * (lam * trp + T(2) * mu * pxx);
+        out[1] = hphi * (lam * trp + T(2) * mu * pyy);
+        out[2] = hphi * (T(2) * mu * pxy);
+    }
+}
+
+}  // namespace pff

@@ -1,0 +1,21 @@
+// Column kernels (FFT along y, mode multiplier, inverse FFT along y) for one precision (PFF_REAL).
+#include "kernels.cuh"
+
+namespace pff {
+
+template <typename T>
+void launch_col(int op, int nx, int ny, int wp, const Desc<T>* d, int np, cudaStream_t st) {
+    (void)nx;
+    switch (op) {
+        case CO_GAMMA_N: PFF_SIZE_SWITCH(ny, (go_col<T, N_, 3, FColGammaN>(d, np, wp, st, FAM_COL * 16 + op))); break;
+        case CO_GAMMA_CG: PFF_SIZE_SWITCH(ny, (go_col<T, N_, 3, FColGammaCG>(d, np, wp, st, FAM_COL * 16 + op))); break;
+        case CO_GAMMA_PLAIN: PFF_SIZE_SWITCH(ny, (go_col<T, N_, 3, FColGammaPlain>(d, np, wp, st, FAM_COL * 16 + op))); break;
+        case CO_LAP_DF: PFF_SIZE_SWITCH(ny, (go_col<T, N_, 1, FColLapDF>(d, np, wp, st, FAM_COL * 16 + op))); break;
+        case CO_LAP_PF: PFF_SIZE_SWITCH(ny, (go_col<T, N_, 1, FColLapPF>(d, np, wp, st, FAM_COL * 16 + op))); break;
+        case CO_LAP_PLAIN: PFF_SIZE_SWITCH(ny, (go_col<T, N_, 1, FColLapPlain>(d, np, wp, st, FAM_COL * 16 + op))); break;
+        default: break;
+    }
+}
+template void launch_col<PFF_REAL>(int, int, int, int, const Desc<PFF_REAL>*, int, cudaStream_t);
+
+}  // namespace pff

@@ -1,0 +1,566 @@
+// ops.cuh -- per-pixel prologues / epilogues / finalizers of the load step.
+//
+// Mechanics (Sec. 3.1.1), one operator application per CG iteration:
+//   K1 row_fwd  FCgIn     : x += a p, r -= a q, p = r + b p (previous iteration's a, b);
+//                           r.r (FP64 sum); tau = C_m : p; FFT rows
+//   K2 col      FColGamma : Gamma projection between column FFTs
+//   K3 row_inv  FCgOut    : q = A p; p.q, r.q, q.q -> a = r.r/p.q,
+//                           r'.r' = r.r - 2a r.q + a^2 q.q, b = r'.r'/r.r
+// Newton residual (Eq. elasticity_nodal): FNewtonIn / FColGammaN / FNewtonOut.
+// Phase field (Algorithm 1), two operator applications per BCCG iteration:
+//   A1 FPfA1 (p = -r + b p, masked) -> A2 lap -> A3 FPfA3 (p.Jp, r.p -> alpha)
+//   B1 FPfB1 (v = max(v + alpha p, v_con)) -> B2 lap -> B3 FPfB3 (r = Jv - b, active set,
+//   r.r, r.r_old -> beta, convergence).
+// Flags: see Ctrl in common.cuh.
+#pragma once
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace pff {
+
+template <typename T>
+__device__ __forceinline__ void lame_at(const Desc<T>& d, size_t i, T& lam, T& mu) {
+    T E = d.E[i];
+    lam = T(d.k.lam_c) * E;
+    mu = T(d.k.mu_c) * E;
+}
+template <typename T> __device__ __forceinline__ T hdeg(T phi) { return (T(1) - phi) * (T(1) - phi); }
+
+// weighted (Frobenius) inner product of symmetric tensors stored (xx, yy, xy)
+template <typename T>
+__device__ __forceinline__ void wdot(Acc<T>& a, T x0, T x1, T x2, T y0, T y1, T y2) {
+    a.addp(x0, y0);
+    a.addp(x1, y1);
+    a.addp(x2 + x2, y2);
+}
+
+struct NoCtx {};
+
+// ---------------------------------------------------------------- mechanics
+template <typename T>
+struct FNewtonIn {   // eps* += theta (rounds > 0), sigma(eps_bar + eps*, phi)
+    static constexpr int NR = 0;
+    struct Ctx { T eb[3]; int fold; int split; };
+    __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->nd_a); }
+    __device__ static Ctx prep(const Desc<T>& d) {
+        Ctx c;
+        for (int k = 0; k < 3; ++k) c.eb[k] = T(ldd(&d.ctrl->eps_bar[k]));
+        c.fold = ldflag(&d.ctrl->newton_it) > 0;
+        c.split = d.k.split;
+        return c;
+    }
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[3], Acc<T>*) {
+        T e0 = d.eps[0][i], e1 = d.eps[1][i], e2 = d.eps[2][i];
+        if (c.fold) {
+            e0 += d.th[0][i]; e1 += d.th[1][i]; e2 += d.th[2][i];
+            d.eps[0][i] = e0; d.eps[1][i] = e1; d.eps[2][i] = e2;
+        }
+        T lam, mu;
+        lame_at(d, i, lam, mu);
+        stress(c.split, c.eb[0] + e0, c.eb[1] + e1, c.eb[2] + e2, hdeg(d.phi[i]), lam, mu, v);
+    }
+    __device__ static void finalize(const Desc<T>&, const double*) {}
+};
+
+struct FColGammaN {   // Newton trio column pass: copies nd_b = nd_a
+    template <typename T> __device__ static bool skip(const Desc<T>& d) {
+        int f = ldflag(&d.ctrl->nd_a);
+        if (blockIdx.x == 0 && threadIdx.x == 0) d.ctrl->nd_b = f;
+        return f;
+    }
+    template <typename T> __device__ static void apply(const Desc<T>& d, int kx, int ky, typename CT<T>::t (&v)[3]) {
+        gamma_apply(d, kx, ky, v);
+    }
+};
+
+template <typename T>
+struct FNewtonOut {   // R = P sigma; CG start r = p = -R, theta = 0; Newton test
+    static constexpr int NR = 1;
+    using Ctx = NoCtx;
+    __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->nd_b); }
+    __device__ static Ctx prep(const Desc<T>&) { return Ctx{}; }
+    __device__ static void pixel(const Desc<T>& d, const Ctx&, size_t i, T (&v)[3], Acc<T>* acc) {
+        wdot(acc[0], v[0], v[1], v[2], v[0], v[1], v[2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            d.r[k][i] = -v[k];
+            d.p[k][i] = -v[k];
+            d.th[k][i] = T(0);
+        }
+    }
+    __device__ static void finalize(const Desc<T>& d, const double* tot) {
+        Ctrl* c = d.ctrl;
+        const Consts& k = d.k;
+        double R2 = tot[0], rn = sqrt(R2);
+        // ||C_0(E) : eps_bar|| = sqrt(sum E^2) * |C_0(1) : eps_bar|
+        double eb0 = c->eps_bar[0], eb1 = c->eps_bar[1], eb2 = c->eps_bar[2];
+        double tr = eb0 + eb1;
+        double s0 = k.lam_c * tr + 2.0 * k.mu_c * eb0, s1 = k.lam_c * tr + 2.0 * k.mu_c * eb1, s2 = 2.0 * k.mu_c * eb2;
+        double target = k.mech_tol * sqrt(c->sumE2) * sqrt(s0 * s0 + s1 * s1 + 2.0 * s2 * s2);
+        c->mech_target = target;
+        c->R2 = R2;
+        if (rn <= target || c->newton_it >= k.max_newton) {
+            if (rn > target) c->status |= 1;
+            c->nd_a = 1;
+            c->cg_a = 1;
+            c->cg_b = 1;
+        } else {
+            const bool linear = (k.split != SPECTRAL);
+            c->cg_target = linear ? target : fmax(target, k.mech_cg_rtol * rn);
+            c->rr = R2;
+            c->cg_it = 0;
+            c->cg_break = 0;
+            c->cg_a = 0;
+            c->cg_b = 0;
+            c->newton_it += 1;
+            if (linear) {   // a linear model takes one Newton step (Sec. 3.1.1)
+                c->nd_a = 1;
+                c->needs_fold = 1;
+            }
+        }
+    }
+};
+
+template <typename T>
+struct FCgIn {
+    static constexpr int NR = 1;
+    struct Ctx { T alpha, beta; int upd; T eb[3]; int split; };
+    __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->cg_a); }
+    __device__ static Ctx prep(const Desc<T>& d) {
+        Ctx c;
+        c.upd = ldflag(&d.ctrl->cg_it) > 0;
+        c.alpha = T(ldd(&d.ctrl->alpha));
+        c.beta = T(ldd(&d.ctrl->beta));
+        for (int k = 0; k < 3; ++k) c.eb[k] = T(ldd(&d.ctrl->eps_bar[k]));
+        c.split = d.k.split;
+        return c;
+    }
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[3], Acc<T>* acc) {
+        T r[3], p[3];
+        if (c.upd) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                T pk = d.p[k][i];
+                T rk = d.r[k][i] - c.alpha * d.q[k][i];
+                d.th[k][i] += c.alpha * pk;
+                pk = rk + c.beta * pk;
+                d.r[k][i] = rk;
+                d.p[k][i] = pk;
+                r[k] = rk;
+                p[k] = pk;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) { r[k] = d.r[k][i]; p[k] = d.p[k][i]; }
+        }
+        wdot(acc[0], r[0], r[1], r[2], r[0], r[1], r[2]);
+        T lam, mu;
+        lame_at(d, i, lam, mu);
+        tangent(c.split, c.eb[0] + d.eps[0][i], c.eb[1] + d.eps[1][i], c.eb[2] + d.eps[2][i],
+                hdeg(d.phi[i]), lam, mu, p[0], p[1], p[2], v);
+    }
+    __device__ static void finalize(const Desc<T>& d, const double* tot) {
+        Ctrl* c = d.ctrl;
+        double rr = tot[0];
+        c->rr = rr;
+        bool conv = sqrt(rr) <= c->cg_target;
+        if (conv || c->cg_it >= d.k.max_cg || c->cg_break) {
+            if (!conv && !c->cg_break) c->status |= 1;
+            c->cg_b = 1;
+        } else {
+            c->cg_b = 0;
+        }
+    }
+};
+
+struct FColGammaCG {   // CG column pass: copies cg_a = cg_b
+    template <typename T> __device__ static bool skip(const Desc<T>& d) {
+        int f = ldflag(&d.ctrl->cg_b);
+        if (blockIdx.x == 0 && threadIdx.x == 0) d.ctrl->cg_a = f;
+        return f;
+    }
+    template <typename T> __device__ static void apply(const Desc<T>& d, int kx, int ky, typename CT<T>::t (&v)[3]) {
+        gamma_apply(d, kx, ky, v);
+    }
+};
+
+template <typename T>
+struct FCgOut {
+    static constexpr int NR = 3;
+    using Ctx = NoCtx;
+    __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->cg_b); }
+    __device__ static Ctx prep(const Desc<T>&) { return Ctx{}; }
+    __device__ static void pixel(const Desc<T>& d, const Ctx&, size_t i, T (&v)[3], Acc<T>* acc) {
+        T p0 = d.p[0][i], p1 = d.p[1][i], p2 = d.p[2][i];
+        T r0 = d.r[0][i], r1 = d.r[1][i], r2 = d.r[2][i];
+        d.q[0][i] = v[0]; d.q[1][i] = v[1]; d.q[2][i] = v[2];
+        wdot(acc[0], p0, p1, p2, v[0], v[1], v[2]);
+        wdot(acc[1], r0, r1, r2, v[0], v[1], v[2]);
+        wdot(acc[2], v[0], v[1], v[2], v[0], v[1], v[2]);
+    }
+    __device__ static void finalize(const Desc<T>& d, const double* tot) {
+        Ctrl* c = d.ctrl;
+        double pAp = tot[0];
+        c->pAp = pAp; c->rAp = tot[1]; c->qq = tot[2];
+        if (!(pAp > 0.0)) {
+            c->cg_break = 1;
+            c->alpha = 0.0;
+            c->beta = 0.0;
+        } else {
+            double rr = c->rr;
+            double a = rr / pAp;
+            double rn = rr - 2.0 * a * tot[1] + a * a * tot[2];
+            if (rn < 0.0) rn = 0.0;
+            c->alpha = a;
+            c->beta = rr > 0.0 ? rn / rr : 0.0;
+        }
+        c->cg_it += 1;
+        c->cg_total += 1;
+    }
+};
+
+// elementwise: eps* += theta after a linear model's single Newton step
+template <typename T>
+struct FFold {
+    static constexpr int NR = 0;
+    using Ctx = NoCtx;
+    __device__ static bool skip(const Desc<T>& d) { return !ldflag(&d.ctrl->needs_fold); }
+    __device__ static Ctx prep(const Desc<T>&) { return Ctx{}; }
+    __device__ static void pixel(const Desc<T>& d, const Ctx&, size_t i, Acc<T>*) {
+        d.eps[0][i] += d.th[0][i];
+        d.eps[1][i] += d.th[1][i];
+        d.eps[2][i] += d.th[2][i];
+    }
+    __device__ static void finalize(const Desc<T>&, const double*) {}
+};
+
+// ---------------------------------------------------------------- scalar-field transforms
+template <typename T>
+struct FPhiIn {   // input phi (driving force and energy trios)
+    static constexpr int NR = 0;
+    using Ctx = NoCtx;
+    __device__ static bool skip(const Desc<T>&) { return false; }
+    __device__ static Ctx prep(const Desc<T>&) { return Ctx{}; }
+    __device__ static void pixel(const Desc<T>& d, const Ctx&, size_t i, T (&v)[1], Acc<T>*) { v[0] = d.phi[i]; }
+    __device__ static void finalize(const Desc<T>&, const double*) {}
+};
+
+struct FColLapDF {   // column pass of the step's lap(phi); clears needs_fold (read by the fold kernel before)
+    template <typename T> __device__ static bool skip(const Desc<T>& d) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) d.ctrl->needs_fold = 0;
+        return false;
+    }
+    template <typename T> __device__ static void apply(const Desc<T>& d, int kx, int ky, typename CT<T>::t (&v)[1]) {
+        lap_apply(d, kx, ky, v);
+    }
+};
+
+struct FColLapPlain {
+    template <typename T> __device__ static bool skip(const Desc<T>&) { return false; }
+    template <typename T> __device__ static void apply(const Desc<T>& d, int kx, int ky, typename CT<T>::t (&v)[1]) {
+        lap_apply(d, kx, ky, v);
+    }
+};
+
+struct FColGammaPlain {
+    template <typename T> __device__ static bool skip(const Desc<T>&) { return false; }
+    template <typename T> __device__ static void apply(const Desc<T>& d, int kx, int ky, typename CT<T>::t (&v)[3]) {
+        gamma_apply(d, kx, ky, v);
+    }
+};
+
+template <typename T>
+struct FLapOut {   // lap = nabla^2_N phi
+    static constexpr int NR = 0;
+    using Ctx = NoCtx;
+    __device__ static bool skip(const Desc<T>&) { return false; }
+    __device__ static Ctx prep(const Desc<T>&) { return Ctx{}; }
+    __device__ static void pixel(const Desc<T>& d, const Ctx&, size_t i, T (&v)[1], Acc<T>*) { d.lap[i] = v[0]; }
+    __device__ static void finalize(const Desc<T>&, const double*) {}
+};
+
+template <typename T>
+struct FEnergyOut {   // F_f = c sum (f(phi) - ell^2 phi lap phi) dA (Eq. Ff with Parseval)
+    static constexpr int NR = 1;
+    using Ctx = NoCtx;
+    __device__ static bool skip(const Desc<T>&) { return false; }
+    __device__ static Ctx prep(const Desc<T>&) { return Ctx{}; }
+    __device__ static void pixel(const Desc<T>& d, const Ctx&, size_t i, T (&v)[1], Acc<T>* acc) {
+        T ph = d.phi[i];
+        T f = d.k.fracture == AT1 ? ph : ph * ph;
+        acc[0].add(f);
+        acc[0].addp(-T(d.k.ell2) * ph, v[0]);
+    }
+    __device__ static void finalize(const Desc<T>& d, const double* tot) {
+        d.ctrl->Ff = d.k.c * tot[0] * d.k.dA;
+    }
+};
+
+// copies for the operator entry points: input r[], output q[]
+template <typename T, int NC>
+struct FCopyIn {
+    static constexpr int NR = 0;
+    using Ctx = NoCtx;
+    __device__ static bool skip(const Desc<T>&) { return false; }
+    __device__ static Ctx prep(const Desc<T>&) { return Ctx{}; }
+    __device__ static void pixel(const Desc<T>& d, const Ctx&, size_t i, T (&v)[NC], Acc<T>*) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) v[k] = d.r[k][i];
+    }
+    __device__ static void finalize(const Desc<T>&, const double*) {}
+};
+template <typename T, int NC>
+struct FCopyOut {
+    static constexpr int NR = 0;
+    using Ctx = NoCtx;
+    __device__ static bool skip(const Desc<T>&) { return false; }
+    __device__ static Ctx prep(const Desc<T>&) { return Ctx{}; }
+    __device__ static void pixel(const Desc<T>& d, const Ctx&, size_t i, T (&v)[NC], Acc<T>*) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) d.q[k][i] = v[k];
+    }
+    __device__ static void finalize(const Desc<T>&, const double*) {}
+};
+
+// ---------------------------------------------------------------- phase field
+// BCCG start (Algorithm 1 lines 1-5) after the rescale of lines 4-10 of Algorithm 4:
+// eps <- gamma eps; a = eta/dt + 2 psi_0^+ + c f''; b = -F_phi(phi_n);
+// v_con = phi_con(phi_n) - phi_n <= 0; v^0 = 0; r^0 = -b masked; p^0 = -r^0.
+template <typename T>
+struct FPfInit {
+    static constexpr int NR = 2;
+    struct Ctx { double g; int resc; double eb[3]; };
+    __device__ static bool skip(const Desc<T>&) { return false; }
+    __device__ static Ctx prep(const Desc<T>& d) {
+        Ctx c;
+        c.g = ldd(&d.ctrl->gamma);
+        c.resc = ldflag(&d.ctrl->rescaled);
+        for (int k = 0; k < 3; ++k) c.eb[k] = c.g * ldd(&d.ctrl->eps_bar[k]);
+        return c;
+    }
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, Acc<T>* acc) {
+        const Consts& k = d.k;
+        T e0 = d.eps[0][i], e1 = d.eps[1][i], e2 = d.eps[2][i];
+        if (c.resc) {
+            T g = T(c.g);
+            e0 *= g; e1 *= g; e2 *= g;
+            d.eps[0][i] = e0; d.eps[1][i] = e1; d.eps[2][i] = e2;
+        }
+        double E = (double)d.E[i];
+        double lam = k.lam_c * E, mu = k.mu_c * E;
+        double psi = psi_plus<double>(k.split, c.eb[0] + (double)e0, c.eb[1] + (double)e1, c.eb[2] + (double)e2, lam, mu);
+        T ph = d.phi[i];
+        double phd = (double)ph;
+        double fp = k.fracture == AT1 ? 1.0 : 2.0 * phd;
+        T a = T(k.eta_dt + 2.0 * psi + k.cf2);
+        T b = T(2.0 * (1.0 - phd) * psi - k.c * fp + k.kappa * (double)d.lap[i]);
+        T pcon = (k.irrev == CRACK_SET) ? (ph >= T(k.crack_thr) ? ph : T(0)) : ph;
+        T vcon = pcon - ph;
+        T v = T(0) < vcon ? vcon : T(0);
+        bool at = (v == vcon);
+        T r = -b;
+        bool active = at && (r > T(0));
+        if (active) r = T(0);
+        d.th[0][i] = v;
+        d.th[1][i] = r;
+        d.th[2][i] = -r;
+        d.r[0][i] = a;
+        d.r[1][i] = b;
+        d.r[2][i] = vcon;
+        d.flags[i] = (uint8_t)((at ? 1 : 0) | (active ? 2 : 0));
+        acc[0].addp(r, r);
+        acc[1].addp(b, b);
+    }
+    __device__ static void finalize(const Desc<T>& d, const double* tot) {
+        Ctrl* c = d.ctrl;
+        const Consts& k = d.k;
+        double rn = sqrt(tot[0]);
+        double target = fmax(fmax(k.pf_tol * rn, k.pf_atol), k.pf_floor * sqrt(tot[1]));
+        c->pf_rr = tot[0];
+        c->pf_target = target;
+        c->pf_it = 0;
+        c->pf_break = 0;
+        c->n_active = 0;
+        int done = rn <= target;
+        c->pf_a = done;
+        c->pf_b = done;
+        if (c->rescaled)
+            for (int j = 0; j < 3; ++j) c->eps_bar[j] *= c->gamma;
+    }
+};
+
+template <typename T>
+struct FPfA1 {   // p = -r + beta p, zero on the active set; input p
+    static constexpr int NR = 0;
+    struct Ctx { T beta; int upd; };
+    __device__ static bool skip(const Desc<T>& d) {
+        int f = ldflag(&d.ctrl->pf_b);
+        if (blockIdx.x == 0 && threadIdx.x == 0) d.ctrl->pf_a = f;
+        return f;
+    }
+    __device__ static Ctx prep(const Desc<T>& d) {
+        Ctx c;
+        c.upd = ldflag(&d.ctrl->pf_it) > 0;
+        c.beta = T(ldd(&d.ctrl->pf_beta));
+        return c;
+    }
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[1], Acc<T>*) {
+        T p = d.th[2][i];
+        if (c.upd) {
+            p = -d.th[1][i] + c.beta * p;
+            if (d.flags[i] & 2) p = T(0);
+            d.th[2][i] = p;
+        }
+        v[0] = p;
+    }
+    __device__ static void finalize(const Desc<T>&, const double*) {}
+};
+
+struct FColLapPF {
+    template <typename T> __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
+    template <typename T> __device__ static void apply(const Desc<T>& d, int kx, int ky, typename CT<T>::t (&v)[1]) {
+        lap_apply(d, kx, ky, v);
+    }
+};
+
+template <typename T>
+struct FPfA3 {   // J p; p.Jp, r.p -> alpha = -(r.p)/(p.Jp)
+    static constexpr int NR = 2;
+    struct Ctx { T kappa; };
+    __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
+    __device__ static Ctx prep(const Desc<T>& d) { return Ctx{T(d.k.kappa)}; }
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[1], Acc<T>* acc) {
+        T p = d.th[2][i];
+        T Jp = d.r[0][i] * p - c.kappa * v[0];
+        acc[0].addp(p, Jp);
+        acc[1].addp(d.th[1][i], p);
+    }
+    __device__ static void finalize(const Desc<T>& d, const double* tot) {
+        Ctrl* c = d.ctrl;
+        c->pJp = tot[0];
+        c->pf_rp = tot[1];
+        if (!(tot[0] > 0.0)) {
+            c->pf_break = 1;
+            c->pf_alpha = 0.0;
+        } else {
+            c->pf_alpha = -tot[1] / tot[0];
+        }
+    }
+};
+
+template <typename T>
+struct FPfB1 {   // v = max(v + alpha p, v_con); bound flag; input v
+    static constexpr int NR = 0;
+    struct Ctx { T alpha; };
+    __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
+    __device__ static Ctx prep(const Desc<T>& d) { return Ctx{T(ldd(&d.ctrl->pf_alpha))}; }
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[1], Acc<T>*) {
+        T x = d.th[0][i] + c.alpha * d.th[2][i];
+        T vc = d.r[2][i];
+        if (x < vc) x = vc;
+        d.th[0][i] = x;
+        d.flags[i] = (uint8_t)(x == vc ? 1 : 0);
+        v[0] = x;
+    }
+    __device__ static void finalize(const Desc<T>&, const double*) {}
+};
+
+template <typename T>
+struct FPfB3 {   // r = Jv - b, active set {bound and r > 0} (sign decided in FP64), beta, convergence
+    static constexpr int NR = 3;
+    struct Ctx { T kappa; double kd; };
+    __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
+    __device__ static Ctx prep(const Desc<T>& d) { return Ctx{T(d.k.kappa), d.k.kappa}; }
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[1], Acc<T>* acc) {
+        T x = d.th[0][i], a = d.r[0][i], b = d.r[1][i], ro = d.th[1][i];
+        T rn = a * x - c.kappa * v[0] - b;
+        uint8_t fl = d.flags[i];
+        bool at = fl & 1;
+        bool pos;
+        if constexpr (sizeof(T) == 8) {
+            pos = rn > T(0);
+        } else {
+            // FP32 residual; decide its sign in FP64 from the same FP32 operands when it is
+            // within rounding of zero (otherwise the FP32 sign is already exact)
+            T mag = fabs(a * x) + fabs(c.kappa * v[0]) + fabs(b);
+            if (fabs(rn) > T(4e-7) * mag) pos = rn > T(0);
+            else pos = ((double)a * (double)x - c.kd * (double)v[0] - (double)b) > 0.0;
+        }
+        bool active = at && pos;
+        if (active) rn = T(0);
+        d.th[1][i] = rn;
+        d.flags[i] = (uint8_t)((at ? 1 : 0) | (active ? 2 : 0));
+        acc[0].addp(rn, rn);
+        acc[1].addp(rn, ro);
+        acc[2].add(active ? T(1) : T(0));
+    }
+    __device__ static void finalize(const Desc<T>& d, const double* tot) {
+        Ctrl* c = d.ctrl;
+        double rr = tot[0];
+        double den = -c->pf_rp;   // = alpha p.Jp
+        c->pf_beta = den != 0.0 ? (rr - tot[1]) / den : 0.0;
+        c->pf_rr = rr;
+        c->pf_it += 1;
+        c->n_active = (int)tot[2];
+        bool conv = sqrt(rr) <= c->pf_target;
+        if (conv || c->pf_it >= d.k.max_pf || c->pf_break) {
+            if (!conv && !c->pf_break) c->status |= 2;
+            c->pf_b = 1;
+        } else {
+            c->pf_b = 0;
+        }
+    }
+};
+
+// Algorithm 4 lines 12-14: phi_{n+1} = phi_n + v, sigma-bar(eps_n, phi_{n+1}), C-bar,
+// ||dphi||_1, F_e, strain increment.
+template <typename T>
+struct FPost {
+    static constexpr int NR = 5;
+    struct Ctx { T eb[3]; };
+    __device__ static bool skip(const Desc<T>&) { return false; }
+    __device__ static Ctx prep(const Desc<T>& d) {
+        Ctx c;
+        for (int k = 0; k < 3; ++k) c.eb[k] = T(ldd(&d.ctrl->eps_bar[k]));
+        return c;
+    }
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, Acc<T>* acc) {
+        T v = d.th[0][i];
+        T ph = d.phi[i] + v;
+        d.phi[i] = ph;
+        T lam, mu;
+        lame_at(d, i, lam, mu);
+        T xx = c.eb[0] + d.eps[0][i], yy = c.eb[1] + d.eps[1][i], xy = c.eb[2] + d.eps[2][i];
+        T h = hdeg(ph);
+        T s[3];
+        stress(d.k.split, xx, yy, xy, h, lam, mu, s);
+        acc[0].add(s[0]);
+        acc[1].add(s[1]);
+        acc[2].add(s[2]);
+        acc[3].add(energy(d.k.split, xx, yy, xy, h, lam, mu));
+        acc[4].add(fabs(v));
+    }
+    __device__ static void finalize(const Desc<T>& d, const double* tot) {
+        Ctrl* c = d.ctrl;
+        const Consts& k = d.k;
+        double sb[3] = {tot[0] * k.inv_n, tot[1] * k.inv_n, tot[2] * k.inv_n};
+        double eb[3] = {c->eps_bar[0], c->eps_bar[1], c->eps_bar[2]};
+        // C-bar at the largest |eps_bar| component, row-major order xx, xy, yy
+        int j = 0;
+        double m = fabs(eb[0]);
+        if (fabs(eb[2]) > m) { j = 2; m = fabs(eb[2]); }
+        if (fabs(eb[1]) > m) { j = 1; m = fabs(eb[1]); }
+        double Cb = eb[j] != 0.0 ? sb[j] / eb[j] : INFINITY;
+        double dphi = k.L1_scale * tot[4];
+        for (int q = 0; q < 3; ++q) { c->sig_bar[q] = sb[q]; c->rep_eps_bar[q] = eb[q]; }
+        c->C_bar = Cb;
+        c->dphi = dphi;
+        c->Fe = tot[3] * k.dA;
+        c->incremented = dphi < k.dphi_min;
+        if (c->incremented)
+            for (int q = 0; q < 3; ++q) c->eps_bar[q] = eb[q] + k.d_eps_bar[q];
+        c->broken = Cb < k.C_broken;
+    }
+};
+
+}  // namespace pff

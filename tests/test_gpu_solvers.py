@@ -1,0 +1,116 @@
+"""Parity of the sub-problem solves and of load steps (C ABI vs FP64 oracle)."""
+import numpy as np
+import pytest
+
+from oracle import constitutive as cm
+from oracle import evolution as ev
+from oracle import mechanics, phasefield
+from oracle.params import AT1, AT2, CRACK_SET, DAMAGE, ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, Params
+from paper_2203_16467_gb300.inputs import eps_M, gaussian_field, modulus_field
+from tests.helpers import bar3, from3, rel_l2, tensor_rel_l2, to3
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pff():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_16467_gb300 import pff as m
+    return m
+
+
+def _phi_field(ny, nx, seed, amp=0.6):
+    z = gaussian_field(ny, nx, 4.0, seed)
+    return amp * (z - z.min()) / (z.max() - z.min())
+
+
+def _gpu_problem(pff, E, prec, par):
+    ny, nx = E.shape
+    p = pff.Problem(nx, ny, prec, E=E)
+    p.set_model(par.fracture, par.split, par.irreversibility)
+    p.set_params(nu=par.nu, Gc=par.Gc, ell=par.ell, dx=par.dx, mech_tol=par.mech_tol, mech_cg_rtol=par.mech_cg_rtol,
+                 pf_tol=par.pf_tol, pf_atol=par.pf_atol, dphi_min=par.dphi_min,
+                 d_eps_bar=(par.d_eps_bar[0][0], par.d_eps_bar[1][1], par.d_eps_bar[0][1]))
+    return p
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("split", [ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE])
+@pytest.mark.parametrize("ny,nx", [(64, 64), (32, 128)])
+def test_mechanics_solve_parity(pff, prec, split, ny, nx):
+    E = modulus_field(ny, nx, 8.0, 3)
+    phi = _phi_field(ny, nx, 4)
+    par = Params(split=split, mech_tol=1e-10, mech_cg_rtol=1e-6)
+    eb = np.array([[0.002, 0.001], [0.001, 0.01]])
+    es_ref, info = mechanics.solve(np.zeros((ny, nx, 2, 2)), eb, phi, E, par)
+    gpar = Params(split=split, mech_tol=1e-10 if prec == 0 else 1e-8, mech_cg_rtol=1e-6)
+    p = _gpu_problem(pff, E, prec, gpar)
+    p.set_phase_field(phi)
+    p.set_strain(None, bar3(eb))
+    rep = p.solve_mechanics()
+    eps = p.get_fields(pff.FIELD_STRAIN)
+    ref = to3(eb[None, None] + es_ref)
+    err = tensor_rel_l2(eps, ref)
+    assert err < (1e-8 if prec == 0 else 1e-5), (err, rep, info)
+    sig = p.get_fields(pff.FIELD_STRESS)
+    lam, mu = cm.lame(E, 0.2)
+    sref = to3(cm.stress(eb[None, None] + es_ref, phi, lam, mu, split))
+    assert tensor_rel_l2(sig, sref) < (1e-8 if prec == 0 else 1e-5)
+    p.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("fracture,irr", [(AT1, CRACK_SET), (AT1, DAMAGE), (AT2, CRACK_SET), (AT2, DAMAGE)])
+def test_phase_field_solve_parity(pff, prec, fracture, irr):
+    ny = nx = 64
+    ell = 2.0
+    E = modulus_field(ny, nx, 8.0, 5)
+    phi0 = _phi_field(ny, nx, 6, amp=0.95)
+    em = eps_M(1.0, 0.2, 1.0, ell)
+    par = Params(fracture=fracture, split=SPECTRAL, irreversibility=irr, ell=ell, mech_tol=1e-10, pf_tol=1e-10,
+                 pf_atol=1e-14)
+    eb = np.array([[0.0, 0.0], [0.0, 1.3 * em]])
+    es, _ = mechanics.solve(np.zeros((ny, nx, 2, 2)), eb, phi0, E, par)
+    lam, mu = cm.lame(E, 0.2)
+    psi = cm.psi_plus(eb[None, None] + es, lam, mu, SPECTRAL)
+    phi_ref, v_ref, info = phasefield.solve(phi0, psi, par)
+    p = _gpu_problem(pff, E, prec, par)
+    p.set_phase_field(phi0)
+    p.set_strain(to3(es), bar3(eb))
+    rep = p.solve_phase_field()
+    phi = p.get_fields(pff.FIELD_PHI)
+    err = rel_l2(phi, phi_ref)
+    assert err < (1e-9 if prec == 0 else 1e-5), (err, rep["bccg_iters"], info["iters"])
+    act = p.get_fields(pff.FIELD_ACTIVE) > 0.5
+    mism = int(np.sum(act != info["active"]))
+    if prec == 0:
+        assert mism == 0
+    else:
+        assert mism <= max(2, act.size // 2000), mism
+    assert phi.min() >= -1e-12
+    p.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_load_steps_parity_32(pff, prec):
+    ny = nx = 32
+    ell = 2.0
+    em = eps_M(1.0, 0.2, 1.0, ell)
+    E = modulus_field(ny, nx, 4.0, 11)
+    par = Params(fracture=AT1, split=SPECTRAL, irreversibility=CRACK_SET, ell=ell, mech_tol=1e-10, pf_tol=1e-10,
+                 pf_atol=1e-14, d_eps_bar=((0.0, 0.0), (0.0, em / 5)))
+    st = ev.State.initial(E)
+    p = _gpu_problem(pff, E, prec, par)
+    nsteps = 40
+    reps = p.step_load(nsteps)
+    assert len(reps) == nsteps
+    for k in range(nsteps):
+        r = ev.load_step(st, par)
+        g = reps[k]
+        np.testing.assert_allclose(g["eps_bar"], bar3(r["eps_bar"]), rtol=1e-6 if prec else 1e-9, atol=1e-12)
+        assert g["incremented"] == r["incremented"]
+        assert g["rescaled"] == r["rescaled"]
+    phi = p.get_fields(pff.FIELD_PHI)
+    assert rel_l2(phi, st.phi) < (1e-7 if prec == 0 else 1e-4)
+    p.close()
