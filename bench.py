@@ -1,0 +1,446 @@
+#!/usr/bin/env python
+"""Benchmark of the staggered phase-field fracture load step on GB300.
+
+Workload (one GPU): eight 512x512 periodic plane-strain grids sharing one
+synthetic Young's modulus field (E = exp(0.3 z)/mean, z Gaussian with
+correlation length 32 px), ell = 4 px, nu = 0.2, G_c = 1, CG tolerance 1e-8,
+one simulation per model variant {AT1, AT2} x {isotropic, strain-spectral} x
+{crack-set, whole-domain irreversibility}, advanced together by the batched
+mixed-precision path (FP32 fields, FP64 reductions).  A step is one
+near-equilibrium load step (Algorithm 4) of all eight simulations.  The
+simulations start from eps_bar_yy = 0.95 eps_M so that every timed step runs
+the mechanics and phase-field solvers.
+
+Metric: pixel-CG-iterations per second (pixels x (mechanics CG + BCCG
+iterations), summed over simulations and GPUs) per unit wall time of the timed
+load steps.  Also reported: load steps per second, p50/p99 step latency, the
+plain per-simulation FP64 GPU path on the same grid, the live roofline of the
+dominant kernel class, an end-to-end number through host buffers and the FP64
+NumPy oracle on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N = 512
+LC = 32.0
+ELL = 4.0
+NU = 0.2
+TOL = 1e-8
+PRELOAD = 0.95
+VARIANTS = [(f, s, i) for f in ("AT1", "AT2") for s in ("ISOTROPIC", "SPECTRAL") for i in ("CRACK_SET", "DAMAGE")]
+WORKLOAD = "grid512_lc32_ell4_8variants_batched_mixed"
+L2_BYTES = 129e6
+FALLBACK_HBM_GBS = 6800.0
+
+
+def eps_m():
+    from paper_2203_16467_gb300.inputs import eps_M
+    return eps_M(1.0, NU, 1.0, ELL)
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d:
+                v = d[k]
+                return float(v["value"] if isinstance(v, dict) else v), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------- oracle sample (CPU)
+def cpu_sample(n_mech, n_bccg):
+    """Time the FP64 oracle on the workload's grid: n_mech mechanics CG iterations and
+    n_bccg BCCG iterations (AT1, strain-spectral, crack set) from the preloaded state.
+    Returns seconds per iteration of each."""
+    from oracle import constitutive as cm
+    from oracle import fourier, mechanics, phasefield
+    from oracle.params import AT1, CRACK_SET, SPECTRAL, Params
+    from paper_2203_16467_gb300.inputs import modulus_field
+    E = modulus_field(N, N, LC, 0)
+    par = Params(fracture=AT1, split=SPECTRAL, irreversibility=CRACK_SET, ell=ELL, nu=NU)
+    lam, mu = cm.lame(E, NU)
+    eb = np.array([[0.0, 0.0], [0.0, 1.2 * eps_m()]])
+    eps = np.broadcast_to(eb, (N, N, 2, 2)).copy()
+    phi = np.zeros((N, N))
+    t0 = time.perf_counter()
+    tang = cm.Tangent(eps, phi, lam, mu, SPECTRAL)
+    R = fourier.project(cm.stress(eps, phi, lam, mu, SPECTRAL)) + 1e-3 * fourier.project(
+        np.random.default_rng(0).standard_normal((N, N, 2, 2)))
+    mechanics.cg(lambda p: fourier.project(tang(p)), -R, 0.0, n_mech)
+    t1 = time.perf_counter()
+    psi = cm.psi_plus(eps, lam, mu, SPECTRAL)
+    b = phasefield.minus_F_phi(phi, psi, par)
+    vcon = phasefield.phi_con(phi, par) - phi
+    phasefield.bccg(lambda x: phasefield.J_apply(x, psi, par), b, vcon, 0.0, 0.0, n_bccg)
+    t2 = time.perf_counter()
+    return (t1 - t0) / n_mech, (t2 - t1) / n_bccg, t2 - t0
+
+
+def run_cpu_sample_subprocess(n_mech, n_bccg):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"print(json.dumps(bench.cpu_sample({n_mech}, {n_bccg})))")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------------- reference arm (oracle)
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    n_mech, n_bccg = 1, 6
+    mech_t, bccg_t = [], []
+    steps = []
+    for s in range(args.warmup + args.steps):
+        tm, tb, tot = cpu_sample(n_mech, n_bccg)
+        if s >= args.warmup:
+            steps.append(tot)
+            mech_t.append(tm)
+            bccg_t.append(tb)
+    total = sum(steps)
+    iters = args.steps * (n_mech + n_bccg)
+    value = iters * N * N / total
+    line = {"impl": "reference", "metric": "pixel_cg_iters_per_s", "value": value, "unit": "pixel-CG-iters/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": N, "reference": "FP64 NumPy oracle (the paper publishes no code)"},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": "pixel-CG-iters/s", "cores": 1,
+                             "sample": f"per step: {n_mech} mechanics CG + {n_bccg} BCCG iterations of the oracle "
+                                       f"on one {N}x{N} AT1 strain-spectral grid (with its tangent setup)"},
+            "e2e": {"value": value, "unit": "pixel-CG-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return line
+
+
+# ------------------------------------------------------------------------- our arm
+def aggregate(elapsed, work, world, device="cpu"):
+    """Replicas only: the slowest rank's time and the work summed over ranks.
+    Returns (max elapsed, [summed work...]); world == 1 returns the inputs."""
+    if world <= 1:
+        return float(elapsed), [float(w) for w in work]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(elapsed)] + [float(w) for w in work], dtype=torch.float64, device=device)
+    tmax = t[:1].clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax.item()), [float(x) for x in t[1:].tolist()]
+
+
+def bytes_per_px(es, nx):
+    """Algorithmic bytes per pixel of each kernel class (family, op) for one problem launch."""
+    s_pc = 2 * es * (nx // 2 + 1) / nx   # half-spectrum bytes per pixel per component
+    return {
+        (0, 1): 26 * es + 3 * s_pc,            # CG update + tangent + row FFT: read th,r,p,q,eps*,phi,E; write th,r,p,S
+        (2, 1): 6 * s_pc,                      # column pass Gamma: read + write S (3 comps)
+        (1, 1): 9 * es + 3 * s_pc,             # row inverse + dots: read S,p,r; write q
+        (0, 3): 3 * es + 1 + s_pc,             # BCCG direction: read r,p,flag; write p,S
+        (2, 4): 2 * s_pc,                      # column pass Laplacian (1 comp)
+        (1, 4): 3 * es + s_pc,                 # J p + dots: read S,p,a,r
+        (0, 4): 4 * es + 1 + s_pc,             # BCCG iterate: read v,p,vcon; write v,flag,S
+        (1, 5): 5 * es + 2 + s_pc,             # residual + active set: read S,v,a,b,r,flag; write r,flag
+    }
+
+
+KERNEL_NAMES = {(0, 1): "row_fwd_cg", (2, 1): "col_gamma_cg", (1, 1): "row_inv_cg", (0, 3): "row_fwd_bccg_dir",
+                (2, 4): "col_lap_bccg", (1, 4): "row_inv_bccg_Jp", (0, 4): "row_fwd_bccg_iter",
+                (1, 5): "row_inv_bccg_resid"}
+
+
+def active_launches(reps_per_problem):
+    """Problem-launches of each kernel class implied by the per-step iteration counts."""
+    cnt = {k: 0 for k in KERNEL_NAMES}
+    for reps in reps_per_problem:
+        for r in reps:
+            cg, nw, pf = r["mech_cg_iters"], r["newton_iters"], r["bccg_iters"]
+            cnt[(0, 1)] += cg + nw
+            cnt[(2, 1)] += cg
+            cnt[(1, 1)] += cg
+            for k in ((0, 3), (2, 4), (1, 4), (0, 4), (1, 5)):
+                cnt[k] += pf if k != (2, 4) else 2 * pf
+    return cnt
+
+
+def make_problems(pff, stream, seed, precision, variants):
+    from paper_2203_16467_gb300.inputs import modulus_field
+    E = modulus_field(N, N, LC, seed)
+    em = eps_m()
+    probs = []
+    for v in variants:
+        p = pff.Problem(N, N, precision, stream=stream, E=E, model=v,
+                        params=dict(nu=NU, ell=ELL, mech_tol=TOL, pf_tol=TOL, d_eps_bar=(0.0, em / 20, 0.0)))
+        p.set_strain(None, (0.0, PRELOAD * em, 0.0))
+        probs.append(p)
+    return probs, E
+
+
+def run_ours(args, rank, world, dev):
+    import torch
+    from paper_2203_16467_gb300 import pff
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()          # non-default stream: the library replays CUDA graphs on it
+    torch.cuda.set_stream(stream)
+    sp = stream.cuda_stream
+    probs, E = make_problems(pff, sp, rank, pff.MIXED, VARIANTS)
+    nprob = len(probs)
+    budget = sum(pff.problem_bytes(N, N, pff.MIXED) for _ in probs)
+    b = pff.create_batch(nprob, budget, sp)
+    for p in probs:
+        assert pff.batch_admit(b, p.h) is not None
+    if args.warmup:
+        pff.batch_step(b, nprob, args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    l0 = pff.kernel_launches()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    reps = [[] for _ in range(nprob)]
+    for s in range(args.steps):
+        out = pff.batch_step(b, nprob, 1)
+        for i in range(nprob):
+            reps[i].extend(out[i])
+        evs[s + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = pff.kernel_launches() - l0
+    clk = clocks.stop()
+    step_ms = [evs[s].elapsed_time(evs[s + 1]) for s in range(args.steps)]
+    # kernel-class durations: CUDA events around every launch, on the batch stream,
+    # over further load steps of the same run (event brackets need direct launches)
+    ki = max(1, min(args.steps, 3))
+    pff.timing_reset()
+    pff.timing_enable(True)
+    reps_k = [[] for _ in range(nprob)]
+    out = pff.batch_step(b, nprob, ki)
+    for i in range(nprob):
+        reps_k[i].extend(out[i])
+    pff.timing_enable(False)
+    elapsed = sum(step_ms) / 1e3
+    mech = sum(r["mech_cg_iters"] for rr in reps for r in rr)
+    bccg = sum(r["bccg_iters"] for rr in reps for r in rr)
+    nsteps_done = sum(len(rr) for rr in reps)
+    # kernel-class timing (live, CUDA events on the batch stream)
+    kt = {k: pff.timing_read(*k) for k in KERNEL_NAMES}
+    acts = active_launches(reps_k)
+    bpp = bytes_per_px(4, N)
+    kernels = {}
+    for k, name in KERNEL_NAMES.items():
+        ms, nl = kt[k]
+        byts = acts[k] * bpp[k] * N * N
+        kernels[name] = {"ms": round(ms, 3), "launches": nl, "share": None,
+                         "achieved_GBs": (byts / (ms / 1e3) / 1e9) if ms > 0 else None,
+                         "alg_bytes_per_launch": byts / nl if nl else None}
+    tot_ms = sum(v["ms"] for v in kernels.values())
+    for v in kernels.values():
+        v["share"] = round(v["ms"] / tot_ms, 4) if tot_ms > 0 else None
+    dom = max(kernels, key=lambda n: kernels[n]["ms"])
+    # distributed aggregation: max time, summed work (no data-path collective)
+    elapsed_max, (mech_all, bccg_all, steps_all) = aggregate(elapsed, [mech, bccg, nsteps_done], world,
+                                                             f"cuda:{dev}")
+    value = (mech_all + bccg_all) * N * N / elapsed_max
+    line = None
+    extra = {}
+    if rank == 0 and not args.no_baselines:
+        extra = baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed)
+    for p in probs:
+        pass
+    pff.destroy_batch(b)
+    if rank == 0:
+        peak, peak_kind = hbm_peak()
+        ach = kernels[dom]["achieved_GBs"]
+        ws = sum(pff.problem_bytes(N, N, pff.MIXED) for _ in probs)
+        line = {
+            "metric": "pixel_cg_iters_per_s", "value": value, "unit": "pixel-CG-iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": N, "simulations_per_gpu": nprob,
+                       "variants": ["/".join(v) for v in VARIANTS], "ell_px": ELL, "lc_px": LC, "nu": NU,
+                       "tol": TOL, "start": f"eps_bar_yy = {PRELOAD} eps_M", "precision": "FP32 fields, FP64 reductions",
+                       "l2": f"inputs larger than L2: device working set {ws / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB",
+                       "parallelism": f"replicas x{world}"},
+            "load_steps_per_s": steps_all / elapsed_max,
+            "mech_pixel_cg_iters_per_s": mech_all * N * N / elapsed_max,
+            "bccg_pixel_iters_per_s": bccg_all * N * N / elapsed_max,
+            "step_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": (ach / peak) if ach else None, "peak_kind": peak_kind, "traffic": None},
+            "kernels": kernels,
+            "kernel_timing": f"CUDA events around each launch on the batch stream, over {ki} further load steps "
+                             f"of the run (direct launches; the timed region replays CUDA graphs)",
+            "clocks": clk,
+        }
+        line.update(extra)
+    return line
+
+
+def baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed):
+    out = {}
+    # plain per-simulation FP64 GPU path: two variants, one at a time, unbatched
+    f_iters, f_steps, f_time = 0, 0, 0.0
+    for v in (VARIANTS[2], VARIANTS[5]):
+        [p64], _ = make_problems(pff, sp, 0, pff.FP64, [v])
+        p64.step_load(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reps = p64.step_load(3)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f_time += e0.elapsed_time(e1) / 1e3
+        f_iters += sum(r["mech_cg_iters"] + r["bccg_iters"] for r in reps)
+        f_steps += len(reps)
+        p64.close()
+    fp64_val = f_iters * N * N / f_time
+    ours_steps = len(probs) * args.steps / elapsed
+    out["plain_fp64_gpu"] = {"pixel_cg_iters_per_s": fp64_val, "load_steps_per_s": f_steps / f_time,
+                             "sample": "AT1/SPECTRAL/CRACK_SET and AT2/ISOTROPIC/DAMAGE, one simulation at a time, "
+                                       "3 load steps each after 1 warm-up step"}
+    out["vs_plain_fp64_gpu"] = {"pixel_cg_iters_per_s": ((mech + bccg) * N * N / elapsed) / fp64_val,
+                                "load_steps_per_s": ours_steps / (f_steps / f_time)}
+    # end to end through the public API with host buffers
+    ke = max(1, min(args.steps, 5))
+    phi_h = np.empty((N, N))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it_e = 0
+    for s in range(ke):
+        for p in probs:
+            p.set_modulus_field(E)
+        out_s = pff.batch_step(b, len(probs), 1)
+        it_e += sum(r["mech_cg_iters"] + r["bccg_iters"] for rr in out_s for r in rr)
+        for p in probs:
+            phi_h = p.get_fields(pff.FIELD_PHI)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    out["e2e"] = {"value": it_e * N * N / te, "unit": "pixel-CG-iters/s",
+                  "h2d_bytes_per_step": len(probs) * N * N * 8, "d2h_bytes_per_step": len(probs) * N * N * 8,
+                  "steps": ke, "path": "pff_set_modulus_field (host E) + pff_batch_step + pff_get_fields(PHI)"}
+    # FP64 oracle on the host cores, same iteration mix as the timed region
+    try:
+        tm, tb, tot = run_cpu_sample_subprocess(8, 80)
+        cpu_time = mech * tm + bccg * tb
+        out["cpu_baseline"] = {"value": (mech + bccg) * N * N / cpu_time, "unit": "pixel-CG-iters/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"oracle timed for 8 mechanics CG + 80 BCCG iterations on one {N}x{N} grid "
+                                         f"({tot:.1f} s; {tm:.3f} s and {tb:.4f} s per iteration), weighted by the "
+                                         f"timed region's mix of {mech} mechanics CG and {bccg} BCCG iterations"}
+    except Exception as e:  # the baseline is reported, never required
+        out["cpu_baseline"] = {"value": None, "unit": "pixel-CG-iters/s", "cores": 1, "kind": "oracle",
+                               "sample": f"failed: {e}"}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-baselines", action="store_true", help="skip the FP64 / e2e / CPU extras")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+        if line:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    line = run_ours(args, rank, world, local)
+    if line:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

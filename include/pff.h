@@ -222,6 +222,11 @@ int pff_batch_step(pff_batch* b, int n_steps, pff_step_report* reports, int* ste
 /* Library-wide counters: kernel launches issued since load (for benchmarks). */
 unsigned long long pff_kernel_launches(void);
 
+/* Replay the fixed per-iteration launch sequences of the CG and BCCG loops
+ * from captured CUDA graphs (default on).  Graphs are used only on problems or
+ * batches created with a non-NULL stream and while kernel timing is off. */
+int pff_set_graphs(int on);
+
 /* Kernel timing for benchmarks.  When enabled, every launch of the library is
  * bracketed by CUDA events on its own stream; pff_timing_read returns the
  * summed device time (ms) and the launch count of one kernel class since the

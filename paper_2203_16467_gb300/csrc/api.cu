@@ -24,7 +24,10 @@
 namespace pff {
 
 static std::atomic<unsigned long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local bool t_capturing = false;
+void count_launch() {
+    if (!t_capturing) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 
 // ---- per-kernel-class event timing
 struct TimingState {
@@ -161,6 +164,23 @@ static size_t problem_bytes(int nx, int ny, int prec) {
 
 static bool valid_n(int n) { return n >= 16 && n <= 2048 && (n & (n - 1)) == 0; }
 
+// CUDA graphs of the two fixed launch sequences of a load step (a chunk of CG
+// iterations, a chunk of BCCG iterations), captured once per group shape.
+struct GraphCache {
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    int nodes[2] = {0, 0};
+    const void* desc = nullptr;
+    int np = 0;
+    void reset() {
+        for (int k = 0; k < 2; ++k) {
+            if (exec[k]) cudaGraphExecDestroy(exec[k]);
+            exec[k] = nullptr;
+            nodes[k] = 0;
+        }
+    }
+};
+
+
 }  // namespace pff
 
 using namespace pff;
@@ -183,7 +203,7 @@ struct pff_problem {
     Ctrl* d_ctrlcopy = nullptr;
     int* h_flags = nullptr;        // pinned
     Ctrl* h_ctrl = nullptr;        // pinned
-    double* h_stage = nullptr;     // pinned staging, 3 n doubles
+    pff::GraphCache graphs;
     double sumE = 0.0, sumE2 = 0.0;
     bool broken = false;
     int flag_host = 0;
@@ -226,7 +246,7 @@ static Consts make_consts(const pff_problem* h) {
     k.mech_cg_rtol = p.mech_cg_rtol;
     k.pf_tol = p.pf_tol;
     k.pf_atol = p.pf_atol;
-    k.pf_floor = mixed ? 2e-6 : 0.0;
+    k.pf_floor = 0.0;
     for (int j = 0; j < 3; ++j) k.d_eps_bar[j] = p.d_eps_bar[j];
     k.dA = p.dx * p.dx;
     k.inv_n = 1.0 / (double)h->n();
@@ -335,9 +355,74 @@ struct Group {
     Ctrl* d_ctrl;          // np
     int* h_flags;          // pinned np
     Ctrl* h_ctrl;          // pinned np
+    GraphCache* graphs;    // may be null (no graphs)
 };
 
 static const int CHUNK = 8;
+static bool g_graphs_enabled = true;
+
+template <typename T>
+static void chunk_direct(int kind, const Group& g) {
+    const Desc<T>* d = (const Desc<T>*)g.d_desc;
+    const int nx = g.nx, ny = g.ny, wp = g.wp, np = g.np;
+    cudaStream_t st = g.st;
+    for (int c = 0; c < CHUNK; ++c) {
+        if (kind == 0) {
+            launch_row_fwd<T>(RF_CG, nx, ny, d, np, st);
+            launch_col<T>(CO_GAMMA_CG, nx, ny, wp, d, np, st);
+            launch_row_inv<T>(RI_CG, nx, ny, d, np, st);
+        } else {
+            launch_row_fwd<T>(RF_PF_A, nx, ny, d, np, st);
+            launch_col<T>(CO_LAP_PF, nx, ny, wp, d, np, st);
+            launch_row_inv<T>(RI_PF_A, nx, ny, d, np, st);
+            launch_row_fwd<T>(RF_PF_B, nx, ny, d, np, st);
+            launch_col<T>(CO_LAP_PF, nx, ny, wp, d, np, st);
+            launch_row_inv<T>(RI_PF_B, nx, ny, d, np, st);
+        }
+    }
+}
+
+// One chunk of iterations: replayed from a captured graph when the group has a
+// graph cache and a non-default stream, and timing is off; launched directly otherwise.
+template <typename T>
+static void run_chunk(int kind, Group& g, bool& warmed) {
+    GraphCache* gc = g.graphs;
+    if (!gc || !g_graphs_enabled || g.st == nullptr || timing_on() || !warmed) {
+        chunk_direct<T>(kind, g);
+        warmed = true;   // attributes (shared-memory opt-in) are set by the first direct chunk
+        return;
+    }
+    if (gc->desc != g.d_desc || gc->np != g.np) {
+        gc->reset();
+        gc->desc = g.d_desc;
+        gc->np = g.np;
+    }
+    if (!gc->exec[kind]) {
+        cudaGraph_t graph = nullptr;
+        t_capturing = true;
+        cudaError_t e = cudaStreamBeginCapture(g.st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            chunk_direct<T>(kind, g);
+            e = cudaStreamEndCapture(g.st, &graph);
+        }
+        t_capturing = false;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gc->exec[kind], graph, 0);
+        if (graph) {
+            size_t n = 0;
+            cudaGraphGetNodes(graph, nullptr, &n);
+            gc->nodes[kind] = (int)n;
+            cudaGraphDestroy(graph);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            gc->exec[kind] = nullptr;
+            chunk_direct<T>(kind, g);
+            return;
+        }
+    }
+    cudaGraphLaunch(gc->exec[kind], g.st);
+    g_launches.fetch_add((unsigned long long)gc->nodes[kind], std::memory_order_relaxed);
+}
 
 template <typename T>
 static int poll(Group& g, bool ctrl_too, pff_problem* eh) {
@@ -365,6 +450,7 @@ static int step_group(Group& g, int max_cg, int max_pf, int max_newton, bool ene
     const int nx = g.nx, ny = g.ny, wp = g.wp, np = g.np;
     cudaStream_t st = g.st;
     int rc;
+    bool warmed = g.graphs && (g.graphs->exec[0] || g.graphs->exec[1]);
     launch_step_begin<T>(d, np, st);
     // mechanics: Newton rounds, each a residual evaluation and a CG solve
     for (int round = 0; round <= max_newton; ++round) {
@@ -372,11 +458,7 @@ static int step_group(Group& g, int max_cg, int max_pf, int max_newton, bool ene
         launch_col<T>(CO_GAMMA_N, nx, ny, wp, d, np, st);
         launch_row_inv<T>(RI_NEWTON, nx, ny, d, np, st);
         for (int it = 0; it <= max_cg + CHUNK; it += CHUNK) {
-            for (int c = 0; c < CHUNK; ++c) {
-                launch_row_fwd<T>(RF_CG, nx, ny, d, np, st);
-                launch_col<T>(CO_GAMMA_CG, nx, ny, wp, d, np, st);
-                launch_row_inv<T>(RI_CG, nx, ny, d, np, st);
-            }
+            run_chunk<T>(0, g, warmed);
             if ((rc = poll<T>(g, false, eh))) return rc;
             if (all_bits(g, 1)) break;
         }
@@ -391,14 +473,7 @@ static int step_group(Group& g, int max_cg, int max_pf, int max_newton, bool ene
     // phase field (Algorithm 1)
     launch_elem<T>(EL_PF_INIT, nx, ny, d, np, st);
     for (int it = 0; it <= max_pf + CHUNK; it += CHUNK) {
-        for (int c = 0; c < CHUNK; ++c) {
-            launch_row_fwd<T>(RF_PF_A, nx, ny, d, np, st);
-            launch_col<T>(CO_LAP_PF, nx, ny, wp, d, np, st);
-            launch_row_inv<T>(RI_PF_A, nx, ny, d, np, st);
-            launch_row_fwd<T>(RF_PF_B, nx, ny, d, np, st);
-            launch_col<T>(CO_LAP_PF, nx, ny, wp, d, np, st);
-            launch_row_inv<T>(RI_PF_B, nx, ny, d, np, st);
-        }
+        run_chunk<T>(1, g, warmed);
         if ((rc = poll<T>(g, false, eh))) return rc;
         if (all_bits(g, 4)) break;
     }
@@ -445,6 +520,7 @@ static Group single_group(pff_problem* h) {
     g.d_ctrl = h->d_ctrlcopy;
     g.h_flags = h->h_flags;
     g.h_ctrl = h->h_ctrl;
+    g.graphs = &h->graphs;
     return g;
 }
 
@@ -486,6 +562,7 @@ struct BatchGroup {
     Ctrl* d_ctrl = nullptr;
     int* h_flags = nullptr;
     Ctrl* h_ctrl = nullptr;
+    GraphCache* graphs = nullptr;
 };
 
 }  // namespace pff
@@ -502,6 +579,7 @@ struct pff_batch {
 namespace pff {
 
 static void free_group(BatchGroup& g) {
+    if (g.graphs) { g.graphs->reset(); delete g.graphs; }
     if (g.d_desc) cudaFree(g.d_desc);
     if (g.d_flags) cudaFree(g.d_flags);
     if (g.d_ctrl) cudaFree(g.d_ctrl);
@@ -528,8 +606,9 @@ static int build_groups(pff_batch* b) {
         for (auto& old : b->groups)
             if (old.d_desc && old.nx == g.nx && old.ny == g.ny && old.prec == g.prec && old.cap >= (int)g.slots.size()) {
                 g.cap = old.cap; g.d_desc = old.d_desc; g.d_flags = old.d_flags; g.d_ctrl = old.d_ctrl;
-                g.h_flags = old.h_flags; g.h_ctrl = old.h_ctrl;
+                g.h_flags = old.h_flags; g.h_ctrl = old.h_ctrl; g.graphs = old.graphs;
                 old.d_desc = nullptr; old.d_flags = nullptr; old.d_ctrl = nullptr; old.h_flags = nullptr; old.h_ctrl = nullptr;
+                old.graphs = nullptr;
                 break;
             }
         if (!g.d_desc) {
@@ -541,6 +620,7 @@ static int build_groups(pff_batch* b) {
             if (e == cudaSuccess) e = cudaMallocHost((void**)&g.h_ctrl, sizeof(Ctrl) * g.cap);
             if (e != cudaSuccess) { free_group(g); b->err = cudaGetErrorString(e); return PFF_ERR_CUDA; }
         }
+        if (!g.graphs) g.graphs = new GraphCache();
         next.push_back(g);
     }
     for (auto& old : b->groups) free_group(old);
@@ -650,6 +730,7 @@ int pff_destroy_problem(pff_problem* h) {
     if (h->d_ctrlcopy) cudaFree(h->d_ctrlcopy);
     if (h->h_flags) cudaFreeHost(h->h_flags);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
+    h->graphs.reset();
     delete h;
     return PFF_OK;
 }
@@ -1017,7 +1098,7 @@ int pff_batch_step(pff_batch* b, int n_steps, pff_step_report* reports, int* ste
             Group g;
             g.nx = bg.nx; g.ny = bg.ny; g.wp = wp_of(bg.nx); g.prec = bg.prec; g.np = (int)bg.slots.size();
             g.st = b->st; g.d_desc = bg.d_desc; g.d_flags = bg.d_flags; g.d_ctrl = bg.d_ctrl;
-            g.h_flags = bg.h_flags; g.h_ctrl = bg.h_ctrl;
+            g.h_flags = bg.h_flags; g.h_ctrl = bg.h_ctrl; g.graphs = bg.graphs;
             rc = run_group_step(g, p, energies, h0);
             if (rc) { b->err = h0->err; return rc; }
             for (size_t j = 0; j < bg.slots.size(); ++j) {
@@ -1034,6 +1115,11 @@ int pff_batch_step(pff_batch* b, int n_steps, pff_step_report* reports, int* ste
 }
 
 unsigned long long pff_kernel_launches(void) { return g_launches.load(); }
+
+int pff_set_graphs(int on) {
+    g_graphs_enabled = on != 0;
+    return PFF_OK;
+}
 
 int pff_timing_enable(int on) {
     cudaDeviceSynchronize();

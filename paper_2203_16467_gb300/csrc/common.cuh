@@ -42,8 +42,8 @@ struct Ctrl {
     double mF_max, D_max, Rf_star, D_star, gamma;
     int istar, flag, rescaled;
     // phase field (Algorithm 1)
-    double pf_rr, pf_rp, pJp, pf_alpha, pf_beta, pf_target;
-    int pf_a, pf_b, pf_it, pf_break, n_active;
+    double pf_rr, pf_rp, pJp, pf_alpha, pf_beta, pf_target, pf_best;
+    int pf_a, pf_b, pf_it, pf_break, n_active, pf_best_it;
     // post-step (Algorithm 4 lines 12-14)
     double rep_eps_bar[3], sig_bar[3], C_bar, dphi, Fe, Ff;
     int incremented, broken;

@@ -81,10 +81,13 @@ __device__ __forceinline__ void stockham_pass(typename CT<T>::t* buf, int s0, in
 }
 
 // NSEQ in-place complex FFTs of length M (unnormalised; forward e^-, inverse e^+).
+// Sequences are processed in rounds of G; each thread holds up to PERMAX
+// radix-4 butterflies of a round in registers (fewer rounds = fewer barriers).
 template <typename T, int M, int NSEQ, int SP, int NT, bool INV>
 __device__ __forceinline__ void fft_smem(typename CT<T>::t* buf, const typename CT<T>::t* twbase) {
     constexpr int LOG = ilog2(M);
-    constexpr int G = cmax(1, cmin(NSEQ, (4 * NT) / M));   // sequences per round
+    constexpr int PERMAX = sizeof(T) == 4 ? 6 : 3;
+    constexpr int G = cmax(1, cmin(NSEQ, (4 * NT * PERMAX) / M));   // sequences per round
     const typename CT<T>::t* tw = twbase + M;
     for (int s0 = 0; s0 < NSEQ; s0 += G) {
         int p = 1;
@@ -101,8 +104,10 @@ __device__ __forceinline__ void fft_smem(typename CT<T>::t* buf, const typename 
 template <typename T, int NX, int NC>
 struct RowCfg {
     static constexpr int M = NX / 2;
-    static constexpr int ROWS = pow2floor(cmax(1, cmin(16, 2048 / (NC * M))));   // divides every ny >= 16
-    static constexpr int NT = (ROWS * NX >= 1024) ? 256 : 128;
+    // rows per block: about 512 complex values per block so that a 512^2 grid
+    // already gives 128+ blocks per component plane
+    static constexpr int ROWS = pow2floor(cmax(1, cmin(16, 512 / (NC * M))));   // divides every ny >= 16
+    static constexpr int NT = (NC * ROWS * M >= 1024) ? 256 : 128;
     static constexpr int SP = M + 1;                        // pitch (complex), odd to spread banks
     static constexpr int NSEQ = NC * ROWS;
     static constexpr size_t SMEM = (size_t)NSEQ * SP * sizeof(typename CT<T>::t);
@@ -112,16 +117,21 @@ template <typename T, int NY, int NC>
 struct ColCfg {
     static constexpr int CSZ = (int)sizeof(typename CT<T>::t);
     static constexpr int CWMIN = 32 / CSZ;                   // one 32-byte sector per row segment
-    static constexpr int CWT = 98304 / (NC * NY * CSZ);
-    static constexpr int CW = CWT >= 16 ? 16 : CWT >= 8 ? 8 : CWT >= 4 ? 4 : CWT >= 2 ? 2 : 1;
-    static constexpr int CWE = cmax(CW, CWMIN);
+    // one 32-byte sector per row segment: enough columns per block for full
+    // sectors, and as many blocks as possible
+    static constexpr int CWE = CWMIN;
     static constexpr int SP = NY + 1;
     static constexpr int NSEQ = NC * CWE;
-    static constexpr int NT = (NSEQ * NY >= 8192) ? 512 : 256;
+    static constexpr int NT = (NSEQ * NY >= 8192) ? 512 : (NSEQ * NY >= 2048 ? 256 : 128);
     static constexpr size_t SMEM = (size_t)NSEQ * SP * CSZ;
 };
 
 constexpr int WP_ALIGN = 16;   // spectral row pitch multiple (largest column tile)
+
+// Staging of M+1 spectrum values per sequence in a buffer of pitch SP = M+1
+// (the in-place FFT layout holds M values; the extra slot lives in the pitch pad).
+template <typename C> __device__ __forceinline__ void stage_store(C* buf, int s, int k, int SP, C v) { buf[s * SP + k] = v; }
+template <typename C> __device__ __forceinline__ C stage_load(const C* buf, int s, int k, int SP) { return buf[s * SP + k]; }
 
 // ---------------------------------------------------------------------------
 // Functor interface (F):
@@ -144,6 +154,7 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_fwd(const Desc<T>
     const typename F::Ctx ctx = F::prep(d);
     constexpr int NRA = F::NR > 0 ? F::NR : 1;
     Acc<T> acc[NRA];
+#pragma unroll 4
     for (int t = threadIdx.x; t < ROWS * NX; t += NT) {
         const int row = t / NX, x = t % NX;
         const size_t pix = (size_t)(y0 + row) * NX + x;
@@ -193,22 +204,39 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
     // complex-to-real pre-processing: Z[k] = A + i B,
     //   A = X[k] + conj(X[M-k]),  B = (X[k] - conj(X[M-k])) e^{+2 pi i k/N}
     // (imaginary parts of X[0] and X[M] are dropped, as for a real inverse).
-    for (int t = threadIdx.x; t < Cfg::NSEQ * M; t += NT) {
-        const int s = t / M, k = t % M;
+    // stage the half spectrum rows in shared memory first (independent loads), then combine
+    for (int t = threadIdx.x; t < Cfg::NSEQ * (M + 1); t += NT) {
+        const int s = t / (M + 1), k = t % (M + 1);
         const int c = s / ROWS, row = s % ROWS;
-        const C* Srow = d.S + c * plane + (size_t)(y0 + row) * d.wp;
-        C xk = Srow[k], xm = Srow[M - k];
-        if (k == 0) { xk.y = T(0); xm.y = T(0); }
-        xm.y = -xm.y;
-        C A = cadd(xk, xm);
-        C B = cmulc(csub(xk, xm), twN[k]);
-        buf[s * SP + k] = C{A.x - B.y, A.y + B.x};
+        stage_store(buf, s, k, SP, d.S[c * plane + (size_t)(y0 + row) * d.wp + k]);
+    }
+    __syncthreads();
+    C z[(Cfg::NSEQ * M + NT - 1) / NT];
+#pragma unroll
+    for (int u = 0; u < (Cfg::NSEQ * M + NT - 1) / NT; ++u) {
+        const int t = threadIdx.x + u * NT;
+        if ((Cfg::NSEQ * M) % NT == 0 || t < Cfg::NSEQ * M) {
+            const int s = t / M, k = t % M;
+            C xk = stage_load<C>(buf, s, k, SP), xm = stage_load<C>(buf, s, M - k, SP);
+            if (k == 0) { xk.y = T(0); xm.y = T(0); }
+            xm.y = -xm.y;
+            C A = cadd(xk, xm);
+            C B = cmulc(csub(xk, xm), twN[k]);
+            z[u] = C{A.x - B.y, A.y + B.x};
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < (Cfg::NSEQ * M + NT - 1) / NT; ++u) {
+        const int t = threadIdx.x + u * NT;
+        if ((Cfg::NSEQ * M) % NT == 0 || t < Cfg::NSEQ * M) buf[(t / M) * SP + t % M] = z[u];
     }
     __syncthreads();
     fft_smem<T, M, Cfg::NSEQ, SP, NT, true>(buf, d.tw);
     const typename F::Ctx ctx = F::prep(d);
     constexpr int NRA = F::NR > 0 ? F::NR : 1;
     Acc<T> acc[NRA];
+#pragma unroll 4
     for (int t = threadIdx.x; t < ROWS * NX; t += NT) {
         const int row = t / NX, x = t % NX;
         const size_t pix = (size_t)(y0 + row) * NX + x;
@@ -239,9 +267,26 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int kx0 = blockIdx.x * CW;
     const size_t plane = (size_t)d.ny * d.wp;
-    for (int t = threadIdx.x; t < NC * NY * CW; t += NT) {
-        const int j = t % CW, ky = (t / CW) % NY, c = t / (CW * NY);
-        buf[(c * CW + j) * SP + ky] = d.S[c * plane + (size_t)ky * d.wp + kx0 + j];
+    constexpr int TOT = NC * NY * CW;
+    constexpr int LPT = (TOT + NT - 1) / NT;   // elements per thread, loaded before any is stored
+    {
+        C tmp[LPT];
+#pragma unroll
+        for (int u = 0; u < LPT; ++u) {
+            const int t = threadIdx.x + u * NT;
+            if (TOT % NT == 0 || t < TOT) {
+                const int j = t % CW, ky = (t / CW) % NY, c = t / (CW * NY);
+                tmp[u] = d.S[c * plane + (size_t)ky * d.wp + kx0 + j];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < LPT; ++u) {
+            const int t = threadIdx.x + u * NT;
+            if (TOT % NT == 0 || t < TOT) {
+                const int j = t % CW, ky = (t / CW) % NY, c = t / (CW * NY);
+                buf[(c * CW + j) * SP + ky] = tmp[u];
+            }
+        }
     }
     __syncthreads();
     fft_smem<T, NY, Cfg::NSEQ, SP, NT, false>(buf, d.tw);
@@ -256,7 +301,8 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
     }
     __syncthreads();
     fft_smem<T, NY, Cfg::NSEQ, SP, NT, true>(buf, d.tw);
-    for (int t = threadIdx.x; t < NC * NY * CW; t += NT) {
+#pragma unroll 4
+    for (int t = threadIdx.x; t < TOT; t += NT) {
         const int j = t % CW, ky = (t / CW) % NY, c = t / (CW * NY);
         d.S[c * plane + (size_t)ky * d.wp + kx0 + j] = buf[(c * CW + j) * SP + ky];
     }

@@ -18,6 +18,8 @@
 
 namespace pff {
 
+constexpr int PF_STALL = 64;    // FP32 BCCG: iterations without a new smallest ||r|| that end a solve
+
 template <typename T>
 __device__ __forceinline__ void lame_at(const Desc<T>& d, size_t i, T& lam, T& mu) {
     T E = d.E[i];
@@ -473,7 +475,9 @@ struct FPfB3 {   // r = Jv - b, active set {bound and r > 0} (sign decided in FP
     __device__ static Ctx prep(const Desc<T>& d) { return Ctx{T(d.k.kappa), d.k.kappa}; }
     __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[1], Acc<T>* acc) {
         T x = d.th[0][i], a = d.r[0][i], b = d.r[1][i], ro = d.th[1][i];
-        T rn = a * x - c.kappa * v[0] - b;
+        T ax = a * x, kl = c.kappa * v[0];
+        T rn = ax - kl - b;
+        T mag = fabs(ax) + fabs(kl) + fabs(b);
         uint8_t fl = d.flags[i];
         bool at = fl & 1;
         bool pos;
@@ -482,7 +486,6 @@ struct FPfB3 {   // r = Jv - b, active set {bound and r > 0} (sign decided in FP
         } else {
             // FP32 residual; decide its sign in FP64 from the same FP32 operands when it is
             // within rounding of zero (otherwise the FP32 sign is already exact)
-            T mag = fabs(a * x) + fabs(c.kappa * v[0]) + fabs(b);
             if (fabs(rn) > T(4e-7) * mag) pos = rn > T(0);
             else pos = ((double)a * (double)x - c.kd * (double)v[0] - (double)b) > 0.0;
         }
@@ -502,7 +505,15 @@ struct FPfB3 {   // r = Jv - b, active set {bound and r > 0} (sign decided in FP
         c->pf_rr = rr;
         c->pf_it += 1;
         c->n_active = (int)tot[2];
-        bool conv = sqrt(rr) <= c->pf_target;
+        // r = Jv - b is recomputed explicitly each iteration, so in FP32 its norm
+        // stalls at the rounding level of that evaluation; an FP32 solve whose
+        // residual has not reached a new minimum for PF_STALL iterations has
+        // converged as far as the arithmetic allows.  FP64 solves use the plain
+        // tolerance test of Algorithm 1.
+        double rn = sqrt(rr);
+        if (c->pf_it == 1 || rn < c->pf_best) { c->pf_best = rn; c->pf_best_it = c->pf_it; }
+        bool stalled = sizeof(T) == 4 && c->pf_it - c->pf_best_it >= PF_STALL;
+        bool conv = rn <= c->pf_target || stalled;
         if (conv || c->pf_it >= d.k.max_pf || c->pf_break) {
             if (!conv && !c->pf_break) c->status |= 2;
             c->pf_b = 1;

@@ -89,6 +89,7 @@ _SIGS = {
     "pff_batch_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(StepReport), _IP]),
     "pff_kernel_launches": (ctypes.c_ulonglong, []),
     "pff_timing_enable": (ctypes.c_int, [ctypes.c_int]),
+    "pff_set_graphs": (ctypes.c_int, [ctypes.c_int]),
     "pff_timing_reset": (ctypes.c_int, []),
     "pff_timing_read": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_ulonglong)]),
 }
@@ -151,6 +152,10 @@ def problem_bytes(nx, ny, precision):
 
 def kernel_launches():
     return int(lib.pff_kernel_launches())
+
+
+def set_graphs(on=True):
+    return _check(lib.pff_set_graphs(1 if on else 0))
 
 
 def timing_enable(on=True):

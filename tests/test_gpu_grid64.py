@@ -1,0 +1,94 @@
+"""The 64x64 workload (AT1, strain-spectral, crack-set irreversibility, ell = 2 px,
+correlation length 8 px, tolerances 1e-8): sub-problem parity at oracle states along
+the whole run, and the whole run's crack set against the oracle's.
+
+The oracle states come from tests/golden/grid64_run.npz, written by
+tests/golden/make_grid64_run.py (oracle only)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import constitutive as cm
+from oracle import mechanics, phasefield
+from paper_2203_16467_gb300.inputs import modulus_field
+from tests.golden.make_grid64_run import LC, N, SEED, params
+from tests.helpers import bar3, rel_l2, tensor_rel_l2, to3
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "grid64_run.npz")
+
+
+@pytest.fixture(scope="module")
+def pff():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_16467_gb300 import pff as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def gold():
+    return np.load(GOLD)
+
+
+def _problem(pff, prec, par, E):
+    p = pff.Problem(N, N, prec, E=E)
+    p.set_model(par.fracture, par.split, par.irreversibility)
+    p.set_params(nu=par.nu, ell=par.ell, mech_tol=par.mech_tol, mech_cg_rtol=par.mech_cg_rtol, pf_tol=par.pf_tol,
+                 pf_atol=par.pf_atol, dphi_min=par.dphi_min,
+                 d_eps_bar=(par.d_eps_bar[0][0], par.d_eps_bar[1][1], par.d_eps_bar[0][1]))
+    return p
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("step", [40, 150, 400, 700, 1000])
+def test_subproblem_parity_along_the_run(pff, gold, prec, step):
+    par = params()
+    E = modulus_field(N, N, LC, SEED)
+    phi = gold[f"phi_{step}"]
+    es0 = gold[f"eps_star_{step}"]
+    eb = gold[f"eps_bar_{step}"]
+    # mechanics solve from the stored warm start
+    es_ref, _ = mechanics.solve(es0, eb, phi, E, par)
+    p = _problem(pff, prec, par, E)
+    p.set_phase_field(phi)
+    p.set_strain(to3(es0), bar3(eb))
+    p.solve_mechanics()
+    eps = p.get_fields(pff.FIELD_STRAIN)
+    err_m = tensor_rel_l2(eps, to3(eb[None, None] + es_ref))
+    assert err_m < (1e-8 if prec == 0 else 1e-5), err_m
+    # phase-field solve from the oracle's strain
+    lam, mu = cm.lame(E, par.nu)
+    psi = cm.psi_plus(eb[None, None] + es_ref, lam, mu, par.split)
+    phi_ref, v_ref, info = phasefield.solve(phi, psi, par)
+    p.set_strain(to3(es_ref), bar3(eb))
+    p.solve_phase_field()
+    phi_gpu = p.get_fields(pff.FIELD_PHI)
+    # relative to the scale of the field in this solve: max(||phi_n||, ||phi_n+1||)
+    # (before the first damage phi_n = 0 and phi_n+1 is the update itself; while
+    # every point stays bound both are 0 and the solve must return exactly 0)
+    scale = max(np.linalg.norm(phi_ref), np.linalg.norm(phi))
+    err_p = float(np.linalg.norm(phi_gpu - phi_ref) / scale) if scale > 0 else float(np.abs(phi_gpu).max())
+    assert err_p < (1e-8 if prec == 0 else 1e-5), err_p
+    act = p.get_fields(pff.FIELD_ACTIVE) > 0.5
+    assert np.array_equal(act, info["active"]), int(np.sum(act != info["active"]))
+    p.close()
+
+
+def _iou(a, b):
+    return np.sum(a & b) / max(1, np.sum(a | b))
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_whole_run_crack_set(pff, gold, prec):
+    par = params()
+    E = modulus_field(N, N, LC, SEED)
+    p = _problem(pff, prec, par, E)
+    reps = p.step_load(5000)
+    assert reps[-1]["broken"]
+    phi = p.get_fields(pff.FIELD_PHI)
+    iou = _iou(phi > 0.95, gold["phi_final"] > 0.95)
+    assert iou >= 0.98, (iou, len(reps), int(gold["n_steps"]))
+    assert phi.min() >= -1e-12 and phi.max() <= 1.0 + 1e-6
+    p.close()
