@@ -219,6 +219,27 @@ int pff_batch_admit(pff_batch* b, pff_problem* h, int* slot);
 int pff_batch_release(pff_batch* b, int slot);
 int pff_batch_step(pff_batch* b, int n_steps, pff_step_report* reports, int* steps_done);
 
+/* Collocation Laplacian without any allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- for
+ * example a framework that has already reserved all device memory for its own
+ * pool, or a latency-critical loop that cannot afford the device-wide
+ * synchronisation an allocation may cause.
+ *   out_dev = nabla^2_N in_dev on an nx x ny periodic grid of spacing dx, both
+ *   FP64 device arrays of nx*ny values (row-major, y slow), owned by the caller.
+ * Scratch (one half spectrum, about 2.2 MB), twiddle table and kernel
+ * descriptor are static device arrays that every GPU loading the library holds
+ * until the process exits.  The first call on a device sets them up (with that
+ * device current): make that first call before any stream capture.  Calls
+ * share the arrays, so calls whose kernels overlap on the GPU (different
+ * streams, or different host threads) race; serialise them.  Nothing in the
+ * scratch needs to start at zero.  Sizes other than powers of two from 16 to
+ * PFF_NOALLOC_MAX_N are rejected with PFF_ERR_INVALID_ARG before any launch;
+ * *err_msg (optional) then points to a static message.  Kernels run on
+ * cuda_stream (may be NULL); the call does not synchronise. */
+#define PFF_NOALLOC_MAX_N 512
+int pff_apply_laplacian_noalloc(int nx, int ny, double dx, const double* in_dev, double* out_dev,
+                                void* cuda_stream, const char** err_msg);
+
 /* Library-wide counters: kernel launches issued since load (for benchmarks). */
 unsigned long long pff_kernel_launches(void);
 

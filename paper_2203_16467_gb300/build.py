@@ -51,8 +51,9 @@ def build(force=False, verbose=False, jobs=None):
         for tag, real in PRECISIONS.items():
             obj = os.path.join(BUILD, tu.replace(".cu", f"_{tag}.o"))
             jobs_list.append([cc, *ARCH, *FLAGS, f"-DPFF_REAL={real}", "-c", os.path.join(CSRC, tu), "-o", obj])
-    api_obj = os.path.join(BUILD, "api.o")
-    jobs_list.append([cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, "api.cu"), "-o", api_obj])
+    for host_tu in ("api.cu", "noalloc.cu"):
+        jobs_list.append([cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, host_tu),
+                          "-o", os.path.join(BUILD, host_tu.replace(".cu", ".o"))])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
