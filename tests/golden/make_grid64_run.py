@@ -7,7 +7,8 @@ and the solver state at the start of a few load steps (checkpoints) so that
 single sub-problem solves on this workload can be compared without re-running
 the oracle from the start.  Calls only oracle/ and the shared input generator.
 
-    python tests/golden/make_grid64_run.py
+    python tests/golden/make_grid64_run.py                       # grid64_run.npz
+    python tests/golden/make_grid64_run.py --tolerance-family    # grid64_tol_family.npz
 """
 import os
 import sys
@@ -29,6 +30,23 @@ def params():
     em = eps_M(1.0, 0.2, 1.0, ELL)
     return Params(fracture=AT1, split=SPECTRAL, irreversibility=CRACK_SET, ell=ELL, nu=0.2,
                   d_eps_bar=((0.0, 0.0), (0.0, em / 20)), mech_tol=1e-8, pf_tol=1e-8)
+
+
+def tolerance_family(tols=(1e-7, 1e-10)):
+    """Final phase fields of the same run at neighbouring solver tolerances: the
+    crack tail of this workload is decided at the tolerance level (two nearby
+    crack tails exist), so whole-run comparisons use this family."""
+    E = modulus_field(N, N, LC, SEED)
+    out = {}
+    for tol in tols:
+        par = params()
+        par.mech_tol = tol
+        par.pf_tol = tol
+        st, reps = ev.run(E, par, max_steps=5000)
+        out[f"phi_final_tol{tol:.0e}"] = st.phi
+        out[f"n_steps_tol{tol:.0e}"] = len(reps)
+    np.savez_compressed(os.path.join(HERE, "grid64_tol_family.npz"), **out)
+    print({k: v for k, v in out.items() if k.startswith("n_steps")})
 
 
 def main():
@@ -56,4 +74,7 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    if "--tolerance-family" in sys.argv:
+        tolerance_family()
+    else:
+        main()
