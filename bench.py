@@ -42,6 +42,7 @@ TOL = 1e-8
 PRELOAD = 0.95
 VARIANTS = [(f, s, i) for f in ("AT1", "AT2") for s in ("ISOTROPIC", "SPECTRAL") for i in ("CRACK_SET", "DAMAGE")]
 WORKLOAD = "grid512_lc32_ell4_8variants_batched_mixed"
+GROUP_SIZE = 1
 L2_BYTES = 129e6
 FALLBACK_HBM_GBS = 6800.0
 
@@ -260,6 +261,9 @@ def run_ours(args, rank, world, dev):
     nprob = len(probs)
     budget = sum(pff.problem_bytes(N, N, pff.MIXED) for _ in probs)
     b = pff.create_batch(nprob, budget, sp)
+    # each simulation on its own stream and host thread: the variants converge at
+    # different iteration counts, and independent progress beats lock-step launches
+    pff.batch_set_group_size(b, GROUP_SIZE)
     for p in probs:
         assert pff.batch_admit(b, p.h) is not None
     if args.warmup:
@@ -288,6 +292,7 @@ def run_ours(args, rank, world, dev):
     # kernel-class durations: CUDA events around every launch, on the batch stream,
     # over further load steps of the same run (event brackets need direct launches)
     ki = max(1, min(args.steps, 3))
+    pff.batch_set_group_size(b, 0)        # one stream: the event brackets of different kernels do not overlap
     pff.timing_reset()
     pff.timing_enable(True)
     reps_k = [[] for _ in range(nprob)]
@@ -295,6 +300,7 @@ def run_ours(args, rank, world, dev):
     for i in range(nprob):
         reps_k[i].extend(out[i])
     pff.timing_enable(False)
+    pff.batch_set_group_size(b, GROUP_SIZE)
     elapsed = sum(step_ms) / 1e3
     mech = sum(r["mech_cg_iters"] for rr in reps for r in rr)
     bccg = sum(r["bccg_iters"] for rr in reps for r in rr)
@@ -336,18 +342,22 @@ def run_ours(args, rank, world, dev):
             "config": {"workload": WORKLOAD, "grid": N, "simulations_per_gpu": nprob,
                        "variants": ["/".join(v) for v in VARIANTS], "ell_px": ELL, "lc_px": LC, "nu": NU,
                        "tol": TOL, "start": f"eps_bar_yy = {PRELOAD} eps_M", "precision": "FP32 fields, FP64 reductions",
+                       "launch_groups": (f"{nprob // GROUP_SIZE} concurrent streams of {GROUP_SIZE} simulation(s)"
+                                         if GROUP_SIZE else "one launch group on one stream"),
                        "l2": f"inputs larger than L2: device working set {ws / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB",
                        "parallelism": f"replicas x{world}"},
             "load_steps_per_s": steps_all / elapsed_max,
             "mech_pixel_cg_iters_per_s": mech_all * N * N / elapsed_max,
             "bccg_pixel_iters_per_s": bccg_all * N * N / elapsed_max,
+            "bccg_clamp_fraction": (sum(r["bccg_clamp_iters"] for rr in reps for r in rr) / bccg) if bccg else None,
             "step_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                          "frac": (ach / peak) if ach else None, "peak_kind": peak_kind, "traffic": None},
             "kernels": kernels,
-            "kernel_timing": f"CUDA events around each launch on the batch stream, over {ki} further load steps "
-                             f"of the run (direct launches; the timed region replays CUDA graphs)",
+            "kernel_timing": f"CUDA events around each launch, over {ki} further load steps of the run with all "
+                             f"eight simulations in one launch group on one stream (direct launches queued behind "
+                             f"a short delay kernel; the timed region replays CUDA graphs on per-simulation streams)",
             "clocks": clk,
         }
         line.update(extra)
@@ -397,6 +407,11 @@ def baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed):
     out["e2e"] = {"value": it_e * N * N / te, "unit": "pixel-CG-iters/s",
                   "h2d_bytes_per_step": len(probs) * N * N * 8, "d2h_bytes_per_step": len(probs) * N * N * 8,
                   "steps": ke, "path": "pff_set_modulus_field (host E) + pff_batch_step + pff_get_fields(PHI)"}
+    # continuous-batching serving: seeded Poisson arrivals of whole simulations
+    try:
+        out["serving"] = serving_run(pff, sp)
+    except Exception as e:
+        out["serving"] = {"error": str(e)[:200]}
     # FP64 oracle on the host cores, same iteration mix as the timed region
     try:
         tm, tb, tot = run_cpu_sample_subprocess(8, 80)
@@ -412,6 +427,23 @@ def baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed):
     return out
 
 
+def serving_run(pff, stream, n_requests=12, rate=40.0, max_steps=20):
+    """Poisson arrivals of simulations with grid sizes uniform over {128^2, 256^2, 512^2,
+    1024^2} and variants uniform over {AT1, AT2} x {isotropic, spectral}, E recipe of the
+    64^2 workload (correlation length 8 px, ell = 2 px), mixed precision, preloaded to
+    0.97 eps_M, each run for max_steps load steps (or until broken); admission by HBM budget."""
+    from paper_2203_16467_gb300 import serving
+    reqs = serving.poisson_requests(n_requests, rate, seed=1234, max_steps=max_steps, preload=0.97, lc=8.0, ell=2.0)
+    server = serving.Server(hbm_budget=8 << 30, max_slots=16, stream=stream)
+    for r in reqs:
+        server.submit(r)
+    st = server.run()
+    server.close()
+    return {"requests": n_requests, "arrival_rate_per_s": rate, "steps_per_request": max_steps,
+            "load_steps_per_s": st["load_steps_per_s"], "step_latency_ms": {k: 1e3 * v for k, v in st["step_latency_s"].items()},
+            "simulation_latency_s": st["sim_latency_s"], "completed": st["completed"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,7 +451,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-baselines", action="store_true", help="skip the FP64 / e2e / CPU extras")
+    ap.add_argument("--group-size", type=int, default=None,
+                    help="simulations per launch group (default 1: one stream per simulation; 0: all in one group)")
     args = ap.parse_args()
+    global GROUP_SIZE
+    if args.group_size is not None:
+        GROUP_SIZE = args.group_size
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -64,10 +64,13 @@ enum {
  * AT2 f = phi^2, c_w = 2 (the form whose optimal profile is Eq. AT2_analytical). */
 enum { PFF_AT1 = 1, PFF_AT2 = 2 };
 
-/* Energy split (Sec. 2.1).  SPECTRAL_STRESSFREE is the non-variational pairing
- * of the strain-spectral crack driving force with the isotropic (stress-free
- * crack) contact model. */
-enum { PFF_ISOTROPIC = 0, PFF_SPECTRAL = 1, PFF_SPECTRAL_STRESSFREE = 2 };
+/* Energy split (Sec. 2.1, Eqs. isotropic_en, strain_spectral_en, vol_dev_en).
+ * SPECTRAL_STRESSFREE and SPECTRAL_VOLDEV are the non-variational pairings of
+ * Sec. 4.2: the strain-spectral crack driving force with the isotropic
+ * (stress-free crack) or the volumetric-deviatoric contact model.  VOLDEV
+ * reads Eq. vol_dev_en with the sums over the two in-plane components and the
+ * 1/3 of the 3-D deviator (the form of the values quoted in Sec. 4.2.1). */
+enum { PFF_ISOTROPIC = 0, PFF_SPECTRAL = 1, PFF_SPECTRAL_STRESSFREE = 2, PFF_VOLDEV = 3, PFF_SPECTRAL_VOLDEV = 4 };
 
 /* Irreversibility (Eq. constraint_field): within the crack set phi >= 0.9, or
  * in the whole domain ("damage"). */
@@ -111,7 +114,18 @@ typedef struct pff_params {
     double crack_set_threshold;/* 0.9 in Eq. constraint_field */
     double d_eps_bar[3];       /* strain increment (xx, yy, xy) */
     int compute_energies;      /* fill F_e and F_f in step reports (one extra scalar FFT pair per step) */
+    int evolution;             /* PFF_NEAR_EQUILIBRIUM (Algorithm 4), PFF_ALTERNATING_MIN (Algorithm 2)
+                                  or PFF_TIME_DEPENDENT (Algorithm 3) */
+    double tol_am;             /* Tol_AM of Algorithm 2 (||dphi||_1 of an inner iteration) */
+    int am_max_inner;          /* cap on the inner iterations of one increment */
+    double dt_min, dt_max;     /* (dt)_min, (dt)_max of Algorithm 3 in units of eta/(G_c/ell) */
+    double dphi_max;           /* (dphi)_max of Algorithm 3 */
 } pff_params;
+
+/* Evolution methods (Sec. 3.2): one pff_step_load step is one pass of the
+ * while-loop of Algorithm 4, one strain increment (outer iteration s) of
+ * Algorithm 2, or one time step n of Algorithm 3. */
+enum { PFF_NEAR_EQUILIBRIUM = 0, PFF_ALTERNATING_MIN = 1, PFF_TIME_DEPENDENT = 2 };
 
 /* Per-load-step report.  eps_bar is the macroscopic strain the step ended
  * with before the increment (after any rescale); sig_bar is the mean stress
@@ -137,6 +151,9 @@ typedef struct pff_step_report {
     int istar;                 /* linear index of argmax -F_phi */
     int broken;                /* C_bar < C_broken */
     int status;                /* PFF_OK or PFF_ERR_NOT_CONVERGED */
+    int bccg_clamp_iters;      /* BCCG iterations in which the projection onto v >= v_con changed v */
+    double dt;                 /* time-dependent method: the time step for the next step (units of eta/(G_c/ell)) */
+    int inner_iters;           /* alternating minimisation: inner iterations; time-dependent: phase-field tries */
 } pff_step_report;
 
 typedef struct pff_problem pff_problem;
@@ -172,8 +189,9 @@ int pff_set_strain(pff_problem* h, const double* eps_star, const double eps_bar[
 /* Reset the near-equilibrium Flag of Algorithm 4 (set once the trigger is met). */
 int pff_set_flag(pff_problem* h, int flag);
 
-/* Run n_steps load steps (Algorithm 4 iterations); out (n_steps entries, may
- * be NULL) receives a report per step.  Stops early, returning the number of
+/* Run n_steps steps of the problem's evolution method (by default load steps,
+ * i.e. Algorithm 4 iterations); out (n_steps entries, may be NULL) receives a
+ * report per step.  Stops early, returning the number of
  * steps done through *steps_done (may be NULL), once C_bar < C_broken.
  * Returns PFF_ERR_NOT_CONVERGED if a sub-solver hit its iteration cap (the
  * state is kept). */
@@ -212,12 +230,18 @@ int pff_constitutive(pff_problem* h, const double* eps3, const double* phi, cons
  * taken.  pff_batch_step runs n_steps load steps of every admitted, not yet
  * broken problem; problems of equal size and precision share every kernel
  * launch.  reports: max_slots * n_steps entries, slot-major (may be NULL);
- * steps_done: max_slots entries (may be NULL). */
+ * steps_done: max_slots entries (may be NULL).  Batches advance near-equilibrium
+ * problems only (admission rejects other evolution methods). */
 int pff_create_batch(int max_slots, size_t hbm_budget, void* cuda_stream, pff_batch** out);
 int pff_destroy_batch(pff_batch* b);
 int pff_batch_admit(pff_batch* b, pff_problem* h, int* slot);
 int pff_batch_release(pff_batch* b, int slot);
 int pff_batch_step(pff_batch* b, int n_steps, pff_step_report* reports, int* steps_done);
+/* Launch grouping of a batch: problems of one shape are split into groups of at
+ * most max_problems_per_group (0, the default: one group per shape).  Each group
+ * shares every kernel launch and advances in lock step; different groups run
+ * on their own streams and host threads and overlap on the device. */
+int pff_batch_set_group_size(pff_batch* b, int max_problems_per_group);
 
 /* Collocation Laplacian without any allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- for

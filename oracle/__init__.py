@@ -23,5 +23,5 @@ Module map:
   phasefield     driving force, Jacobian J, BCCG (Sec. 3.1.2, Algorithm 1)
   evolution      near-equilibrium load step (Algorithm 4), energies, reports
 """
-from .params import Params, AT1, AT2, ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, VOLDEV, CRACK_SET, DAMAGE  # noqa: F401
+from .params import Params, AT1, AT2, ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, VOLDEV, SPECTRAL_VOLDEV, CRACK_SET, DAMAGE  # noqa: F401
 from . import fourier, constitutive, mechanics, phasefield, evolution  # noqa: F401

@@ -14,12 +14,13 @@ Readings of the paper used here:
     the d = 2 in-plane components and the 1/3 of the 3-D deviator (this is the form
     whose value 2 mu (a^2 + ab + 5b^2/18) the paper quotes in Sec. 4.2.1); its stress
     is the exact gradient of that energy.
-  * Non-variational "strain-spectral/stress-free" pairing (Sec. 2.1, Sec. 4.2):
-    driving force psi_0^+ from the spectral split, stress from the isotropic model.
+  * Non-variational pairings (Sec. 2.1, Sec. 4.2): "strain-spectral/stress-free"
+    (driving force psi_0^+ from the spectral split, stress from the isotropic model)
+    and "strain-spectral/vol.-dev." (stress from the volumetric-deviatoric model).
 """
 import numpy as np
 
-from .params import ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, VOLDEV
+from .params import ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, SPECTRAL_VOLDEV, VOLDEV
 
 
 def lame(E, nu):
@@ -125,12 +126,12 @@ def stress_parts(eps, lam, mu, split):
 
 def contact_split(split):
     """Split that supplies the stress (the contact model of Sec. 2.1)."""
-    return ISOTROPIC if split == SPECTRAL_STRESSFREE else split
+    return {SPECTRAL_STRESSFREE: ISOTROPIC, SPECTRAL_VOLDEV: VOLDEV}.get(split, split)
 
 
 def driving_split(split):
     """Split that supplies psi_0^+ in the crack driving force (Sec. 2.1)."""
-    return SPECTRAL if split == SPECTRAL_STRESSFREE else split
+    return SPECTRAL if split in (SPECTRAL_STRESSFREE, SPECTRAL_VOLDEV) else split
 
 
 def stress(eps, phi, lam, mu, split):

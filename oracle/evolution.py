@@ -143,3 +143,74 @@ def run(E, par, max_steps=5000, phi0=None, max_increments=None, stop_when_broken
         if max_increments is not None and n_inc >= max_increments:
             break
     return st, reps
+
+
+# ---------------------------------------------------------------------------
+# Alternating minimisation (Sec. 3.2.1, Algorithm 2) and time-dependent evolution
+# (Sec. 3.2.2, Algorithm 3).  Readings: eta/dt = 0 in the alternating
+# minimisation's phase-field solves (as the algorithm states); the increment's
+# constraint field phi_con(phi_{s,0}) stays fixed over its inner loop; the inner
+# loop ends when ||phi_{s,n+1} - phi_{s,n}||_1 < Tol_AM (the printed "> Tol" is the
+# continuation test); time steps are in units of t~ = eta/(G_c/ell), so
+# eta/dt = (G_c/ell) / dt; the doubling of dt is capped at (dt)_max.
+
+
+def am_increment(st, par, tol_am=1e-3, max_inner=1000):
+    """One strain increment s of Algorithm 2 on state ``st``; returns a report."""
+    lam, mu = cm.lame(st.E, par.nu)
+    st.eps_bar = st.eps_bar + np.asarray(par.d_eps_bar, dtype=float)
+    con = phasefield.phi_con(st.phi, par)            # phi_con(phi_{s,0})
+    inner = 0
+    mech_cg = bccg = 0
+    while True:
+        st.eps_star, minfo = mechanics.solve(st.eps_star, st.eps_bar, st.phi, st.E, par)
+        eps = st.eps_bar[None, None] + st.eps_star
+        psi = cm.psi_plus(eps, lam, mu, par.split)
+        phi_new, v, pinfo = phasefield.solve(st.phi, psi, par, constraint=con, eta_dt=0.0)
+        dphi = (par.dx / par.ell) ** 2 * float(np.sum(np.abs(v)))
+        st.phi = phi_new
+        inner += 1
+        mech_cg += minfo["cg"]
+        bccg += pinfo["iters"]
+        if dphi < tol_am or inner >= max_inner:
+            break
+    sig = cm.stress(eps, st.phi, lam, mu, par.split)
+    sig_bar = sig.mean(axis=(0, 1))
+    C_bar = stiffness(st.eps_bar, sig_bar)
+    C_broken = par.C_broken if par.C_broken is not None else 0.01 * float(st.E.mean())
+    st.n += 1
+    return {"eps_bar": st.eps_bar.copy(), "sig_bar": sig_bar, "C_bar": C_bar, "inner": inner, "dphi_L1": dphi,
+            "mech_cg": mech_cg, "bccg": bccg, "broken": C_bar < C_broken}
+
+
+def td_step(st, par, dt, dt_min=2.0 ** -16, dt_max=2.0 ** 16, dphi_max=1.5):
+    """One time step n of Algorithm 3 on ``st`` with current step ``dt`` (units of
+    t~); returns (report, dt for the next step)."""
+    lam, mu = cm.lame(st.E, par.nu)
+    st.eps_star, minfo = mechanics.solve(st.eps_star, st.eps_bar, st.phi, st.E, par)
+    eps = st.eps_bar[None, None] + st.eps_star
+    psi = cm.psi_plus(eps, lam, mu, par.split)
+    lap_phi = laplacian(st.phi, par.dx)
+    tries = 0
+    while True:
+        eta_dt = (par.Gc / par.ell) / dt
+        phi_new, v, pinfo = phasefield.solve(st.phi, psi, par, lap_phi, eta_dt=eta_dt)
+        dphi = (par.dx / par.ell) ** 2 * float(np.sum(np.abs(v)))
+        tries += 1
+        if dphi < dphi_max or dt <= dt_min:
+            if dphi < dphi_max / 2:
+                dt = min(2.0 * dt, dt_max)
+            break
+        dt = dt / 2.0
+    st.phi = phi_new
+    eps_bar_n = st.eps_bar.copy()
+    incremented = dphi < par.dphi_min and dt >= dt_max
+    if incremented:
+        st.eps_bar = st.eps_bar + np.asarray(par.d_eps_bar, dtype=float)
+    sig_bar = cm.stress(eps, st.phi, lam, mu, par.split).mean(axis=(0, 1))
+    C_bar = stiffness(eps_bar_n, sig_bar)
+    C_broken = par.C_broken if par.C_broken is not None else 0.01 * float(st.E.mean())
+    st.n += 1
+    return ({"eps_bar": eps_bar_n, "sig_bar": sig_bar, "C_bar": C_bar, "dt": dt, "tries": tries, "dphi_L1": dphi,
+             "incremented": incremented, "mech_cg": minfo["cg"], "bccg": pinfo["iters"], "broken": C_bar < C_broken},
+            dt)

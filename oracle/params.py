@@ -9,7 +9,9 @@ tolerances 1e-6, (dphi)_min = 1e-3, (-F_phi)_max = 0.7 G_c/ell,
 from dataclasses import dataclass, field
 
 AT1, AT2 = 1, 2                      # Eq. fracturelocal
-ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, VOLDEV = 0, 1, 2, 3   # Eqs. isotropic_en, strain_spectral_en, vol_dev_en; Sec. 2.1 non-variational pairing
+ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, VOLDEV, SPECTRAL_VOLDEV = 0, 1, 2, 3, 4
+# Eqs. isotropic_en, strain_spectral_en, vol_dev_en; the non-variational pairings of
+# Sec. 4.2 (strain-spectral driving force with the stress-free / vol.-dev. contact model)
 CRACK_SET, DAMAGE = 0, 1             # Eq. constraint_field
 
 

@@ -108,14 +108,23 @@ def bccg(apply_J, b, vcon, rtol, atol, max_iter):
     return v, {"iters": it, "res": float(np.sqrt(np.sum(r * r))), "active": active, "tol": tol}
 
 
-def solve(phi, psi, par, lap_phi=None):
+def solve(phi, psi, par, lap_phi=None, constraint=None, eta_dt=None):
     """One phase-field sub-problem from phi_n with fixed psi_0^+ (Algorithm 1 on Eq. phase_field_update).
 
-    Returns (phi_new, v, info).
+    constraint: the constraining field phi_con (default phi_con(phi_n)); eta_dt:
+    eta/dt of Eq. phase_field_euler (default par.eta_dt()).  Returns (phi_new, v, info).
     """
     if lap_phi is None:
         lap_phi = laplacian(phi, par.dx)
+    if eta_dt is not None:
+        par = _with_eta_dt(par, eta_dt)
     b = minus_F_phi(phi, psi, par, lap_phi)
-    vcon = phi_con(phi, par) - phi
+    pc = phi_con(phi, par) if constraint is None else constraint
+    vcon = pc - phi
     v, info = bccg(lambda x: J_apply(x, psi, par), b, vcon, par.pf_tol, par.pf_atol, par.pf_max_iter)
     return phi + v, v, info
+
+
+def _with_eta_dt(par, eta_dt):
+    import dataclasses
+    return dataclasses.replace(par, eta_over_dt=eta_dt)

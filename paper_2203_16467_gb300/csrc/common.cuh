@@ -21,7 +21,14 @@ template <typename C> __device__ __forceinline__ C cmulc(C a, C b) { return C{a.
 
 // model enums (mirror include/pff.h)
 enum { AT1 = 1, AT2 = 2 };
-enum { ISOTROPIC = 0, SPECTRAL = 1, SPECTRAL_STRESSFREE = 2 };
+enum { ISOTROPIC = 0, SPECTRAL = 1, SPECTRAL_STRESSFREE = 2, VOLDEV = 3, SPECTRAL_VOLDEV = 4 };
+// split that supplies the stress (contact model) / the crack driving force (Sec. 2.1, Sec. 4.2)
+__host__ __device__ __forceinline__ int contact_of(int split) {
+    return split == SPECTRAL_STRESSFREE ? ISOTROPIC : (split == SPECTRAL_VOLDEV ? VOLDEV : split);
+}
+__host__ __device__ __forceinline__ int driving_of(int split) {
+    return (split == SPECTRAL_STRESSFREE || split == SPECTRAL_VOLDEV) ? SPECTRAL : split;
+}
 enum { CRACK_SET = 0, DAMAGE = 1 };
 
 // ---------------------------------------------------------------------------
@@ -43,12 +50,17 @@ struct Ctrl {
     int istar, flag, rescaled;
     // phase field (Algorithm 1)
     double pf_rr, pf_rp, pJp, pf_alpha, pf_beta, pf_target, pf_best;
-    int pf_a, pf_b, pf_it, pf_break, n_active, pf_best_it;
+    int pf_a, pf_b, pf_it, pf_break, n_active, pf_best_it, pf_clamp_iters;
     // post-step (Algorithm 4 lines 12-14)
     double rep_eps_bar[3], sig_bar[3], C_bar, dphi, Fe, Ff;
     int incremented, broken;
     int status;             // bit0: mechanics cap hit, bit1: BCCG cap hit
     unsigned counter;       // last-block reduction counter (reset by the last block)
+    // set by the host for the alternating-minimisation / time-dependent methods
+    double eta_dt_override; // eta/dt of the phase-field step when use_override
+    int use_override;
+    int con_frozen;         // constraint field phi_con taken from aux (fixed over an increment)
+    int post_mode;          // 0: post-step applies Algorithm 4's strain increment; 1: host decides
     int pad;
 };
 
@@ -246,15 +258,37 @@ __device__ __forceinline__ T psi_spectral(T xx, T yy, T xy, T lam, T mu) {
     return T(0.5) * lam * trp * trp + mu * (a1 * a1 + a2 * a2);
 }
 
-// psi_0^+ of the crack-driving-force model (spectral for SPECTRAL and SPECTRAL_STRESSFREE).
+// Volumetric-deviatoric split, Eq. vol_dev_en with the sums over the two in-plane
+// components and the 1/3 of the 3-D deviator; K = lambda + 2 mu / 3.
 template <typename T>
-__device__ __forceinline__ T psi_plus(int split, T xx, T yy, T xy, T lam, T mu) {
-    return split == ISOTROPIC ? psi_iso(xx, yy, xy, lam, mu) : psi_spectral(xx, yy, xy, lam, mu);
+__device__ __forceinline__ T psi_voldev(T xx, T yy, T xy, T lam, T mu) {
+    T tr = xx + yy, K = lam + T(2) * mu / T(3), t3 = tr / T(3);
+    T a = xx - t3, b = yy - t3, trp = rp(tr);
+    return T(0.5) * K * trp * trp + mu * (a * a + b * b + T(2) * xy * xy);
 }
 
-// Stress of the contact model: isotropic for ISOTROPIC and SPECTRAL_STRESSFREE.
+// psi_0^+ of the crack-driving-force model.
+template <typename T>
+__device__ __forceinline__ T psi_plus(int split, T xx, T yy, T xy, T lam, T mu) {
+    const int s = driving_of(split);
+    if (s == ISOTROPIC) return psi_iso(xx, yy, xy, lam, mu);
+    if (s == VOLDEV) return psi_voldev(xx, yy, xy, lam, mu);
+    return psi_spectral(xx, yy, xy, lam, mu);
+}
+
+// Stress of the contact model (isotropic for SPECTRAL_STRESSFREE, vol.-dev. for SPECTRAL_VOLDEV).
 template <typename T>
 __device__ __forceinline__ void stress(int split, T xx, T yy, T xy, T hphi, T lam, T mu, T* s) {
+    split = contact_of(split);
+    if (split == VOLDEV) {
+        // sigma^+ = K <tr>_+ I + 2 mu (eps - 4/9 tr I), sigma^- = K <tr>_- I (exact gradients)
+        T tr = xx + yy, K = lam + T(2) * mu / T(3);
+        T q = T(4) / T(9) * tr;
+        s[0] = hphi * (K * rp(tr) + T(2) * mu * (xx - q)) + K * rm(tr);
+        s[1] = hphi * (K * rp(tr) + T(2) * mu * (yy - q)) + K * rm(tr);
+        s[2] = hphi * (T(2) * mu * xy);
+        return;
+    }
     if (split == SPECTRAL) {
         T sp[3], sm[3], psip;
         spectral_split(xx, yy, xy, lam, mu, sp, sm, psip);
@@ -272,6 +306,11 @@ __device__ __forceinline__ void stress(int split, T xx, T yy, T xy, T hphi, T la
 // Energy density psi = h psi_0^+ + psi_0^- of the contact model (Eq. psi_schema).
 template <typename T>
 __device__ __forceinline__ T energy(int split, T xx, T yy, T xy, T hphi, T lam, T mu) {
+    split = contact_of(split);
+    if (split == VOLDEV) {
+        T tr = xx + yy, K = lam + T(2) * mu / T(3), trm = rm(tr);
+        return hphi * psi_voldev(xx, yy, xy, lam, mu) + T(0.5) * K * trm * trm;
+    }
     if (split == SPECTRAL) {
         Eig2<T> g(xx, yy, xy);
         T a1 = rp(g.e1), a2 = rp(g.e2), b1 = rm(g.e1), b2 = rm(g.e2);
@@ -292,6 +331,15 @@ template <typename T>
 __device__ __forceinline__ void tangent(int split, T xx, T yy, T xy, T hphi, T lam, T mu,
                                         T pxx, T pyy, T pxy, T* out) {
     T trp = pxx + pyy;
+    split = contact_of(split);
+    if (split == VOLDEV) {
+        T K = lam + T(2) * mu / T(3), Ht = hv(xx + yy);
+        T q = T(4) / T(9) * trp;
+        out[0] = hphi * (K * Ht * trp + T(2) * mu * (pxx - q)) + K * (T(1) - Ht) * trp;
+        out[1] = hphi * (K * Ht * trp + T(2) * mu * (pyy - q)) + K * (T(1) - Ht) * trp;
+        out[2] = hphi * (T(2) * mu * pxy);
+        return;
+    }
     if (split == SPECTRAL) {
         Eig2<T> g(xx, yy, xy);
         T dxx, dyy, dxy;

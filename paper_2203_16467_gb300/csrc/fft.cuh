@@ -21,6 +21,13 @@ constexpr int pow2floor(int n) { return n <= 1 ? 1 : 2 * pow2floor(n / 2); }
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
+// Padded index of element e of a sequence in shared memory: one empty slot per
+// 16 elements.  With this padding every read and write pattern of the mixed
+// radix-8/4/2 Stockham passes below touches each 8-byte slot column at most
+// twice per warp (the minimum for 8-byte elements).
+__device__ __forceinline__ int pidx(int e) { return e + (e >> 4); }
+constexpr int padded_len(int M) { return M + M / 16; }
+
 template <typename C, bool INV>
 __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
     C s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
@@ -32,24 +39,51 @@ __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
     a3 = csub(d02, t);
 }
 
+// 8-point DFT in registers: two 4-point DFTs of the even and odd samples and
+// the twiddles W8^k (W8 = exp(-+ 2 pi i / 8)).
+template <typename C, bool INV>
+__device__ __forceinline__ void dft8(C (&u)[8]) {
+    using T = decltype(u[0].x);
+    const T h = T(0.70710678118654752440);
+    C e0 = u[0], e1 = u[2], e2 = u[4], e3 = u[6];
+    C o0 = u[1], o1 = u[3], o2 = u[5], o3 = u[7];
+    dft4<C, INV>(e0, e1, e2, e3);
+    dft4<C, INV>(o0, o1, o2, o3);
+    C t1, t2, t3;
+    if (!INV) {
+        t1 = C{h * (o1.x + o1.y), h * (o1.y - o1.x)};
+        t2 = C{o2.y, -o2.x};
+        t3 = C{h * (o3.y - o3.x), -h * (o3.x + o3.y)};
+    } else {
+        t1 = C{h * (o1.x - o1.y), h * (o1.x + o1.y)};
+        t2 = C{-o2.y, o2.x};
+        t3 = C{-h * (o3.x + o3.y), h * (o3.x - o3.y)};
+    }
+    u[0] = cadd(e0, o0); u[4] = csub(e0, o0);
+    u[1] = cadd(e1, t1); u[5] = csub(e1, t1);
+    u[2] = cadd(e2, t2); u[6] = csub(e2, t2);
+    u[3] = cadd(e3, t3); u[7] = csub(e3, t3);
+}
+
 // One Stockham pass of radix R over sequences [s0, s0+G) of length M stored at
-// buf[s*SP + j]; p = product of the radices of the previous passes.
+// buf[s*SP + pidx(j)]; p = product of the radices of the previous passes.
 //   butterfly i in [0, M/R): k = i mod p; inputs x[i + r M/R]; twiddle
 //   w^(r k) with w = exp(-+2 pi i/(p R)); outputs y[(i - k) R + k + r p].
+// Twiddles: w^k, w^2k (and w^4k for radix 8) from the table, the rest as products.
 template <typename T, int M, int R, int G, int NSEQ, int SP, int NT, bool INV>
 __device__ __forceinline__ void stockham_pass(typename CT<T>::t* buf, int s0, int p, const typename CT<T>::t* tw) {
     using C = typename CT<T>::t;
     constexpr int NBS = M / R;           // butterflies per sequence
     constexpr int NB = G * NBS;          // butterflies in the round
     constexpr int PER = (NB + NT - 1) / NT;
-    C u[PER][R];
+    C u[PER][8];
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         int b = threadIdx.x + j * NT;
         int s = s0 + b / NBS, i = b % NBS;
         if ((NB % NT == 0 || b < NB) && s < NSEQ) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) u[j][r] = buf[s * SP + i + r * NBS];
+            for (int r = 0; r < R; ++r) u[j][r] = buf[s * SP + pidx(i + r * NBS)];
         }
     }
     __syncthreads();
@@ -58,45 +92,80 @@ __device__ __forceinline__ void stockham_pass(typename CT<T>::t* buf, int s0, in
         int b = threadIdx.x + j * NT;
         int s = s0 + b / NBS, i = b % NBS;
         if ((NB % NT == 0 || b < NB) && s < NSEQ) {
-            int k = i & (p - 1);
-            int step = M / (p * R);
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                C w = tw[r * k * step];
-                u[j][r] = INV ? cmulc(u[j][r], w) : cmul(u[j][r], w);
+            const int k = i & (p - 1);
+            if (p > 1) {
+                const int idx = k * (M / (p * R));
+                C w1 = tw[idx];
+                if (INV) w1.y = -w1.y;
+                if (R == 2) {
+                    u[j][1] = cmul(u[j][1], w1);
+                } else {
+                    C w2 = tw[2 * idx];
+                    if (INV) w2.y = -w2.y;
+                    C w3 = cmul(w1, w2);
+                    u[j][1] = cmul(u[j][1], w1);
+                    u[j][2] = cmul(u[j][2], w2);
+                    u[j][3] = cmul(u[j][3], w3);
+                    if (R == 8) {
+                        C w4 = tw[4 * idx];
+                        if (INV) w4.y = -w4.y;
+                        u[j][4] = cmul(u[j][4], w4);
+                        u[j][5] = cmul(u[j][5], cmul(w1, w4));
+                        u[j][6] = cmul(u[j][6], cmul(w2, w4));
+                        u[j][7] = cmul(u[j][7], cmul(w3, w4));
+                    }
+                }
             }
-            if (R == 4) {
+            if (R == 8) {
+                dft8<C, INV>(u[j]);
+            } else if (R == 4) {
                 dft4<C, INV>(u[j][0], u[j][1], u[j][2], u[j][3]);
             } else {
                 C a = u[j][0], c = u[j][1];
                 u[j][0] = cadd(a, c);
                 u[j][1] = csub(a, c);
             }
-            int o = (i - k) * R + k;
+            const int o = (i - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[s * SP + o + r * p] = u[j][r];
+            for (int r = 0; r < R; ++r) buf[s * SP + pidx(o + r * p)] = u[j][r];
         }
     }
     __syncthreads();
 }
 
-// NSEQ in-place complex FFTs of length M (unnormalised; forward e^-, inverse e^+).
-// Sequences are processed in rounds of G; each thread holds up to PERMAX
-// radix-4 butterflies of a round in registers (fewer rounds = fewer barriers).
+// NSEQ in-place complex FFTs of length M (unnormalised; forward e^-, inverse e^+),
+// radix-8 passes after one radix-2 or radix-4 pass when log2 M is not a multiple
+// of 3.  Sequences are processed in rounds of G; each thread holds at most PER8
+// radix-8 butterflies of a round in registers.
 template <typename T, int M, int NSEQ, int SP, int NT, bool INV>
-__device__ __forceinline__ void fft_smem(typename CT<T>::t* buf, const typename CT<T>::t* twbase) {
+__device__ __forceinline__ void fft_smem(typename CT<T>::t* buf, const typename CT<T>::t* tw) {
     constexpr int LOG = ilog2(M);
-    constexpr int PERMAX = sizeof(T) == 4 ? 6 : 3;
-    constexpr int G = cmax(1, cmin(NSEQ, (4 * NT * PERMAX) / M));   // sequences per round
-    const typename CT<T>::t* tw = twbase + M;
+    constexpr int PER8 = sizeof(T) == 4 ? 2 : 1;
+    constexpr int G = cmax(1, cmin(NSEQ, (8 * NT * PER8) / M));   // sequences per round
     for (int s0 = 0; s0 < NSEQ; s0 += G) {
         int p = 1;
-        if (LOG & 1) {
+        if (LOG % 3 == 1) {
             stockham_pass<T, M, 2, G, NSEQ, SP, NT, INV>(buf, s0, 1, tw);
             p = 2;
+        } else if (LOG % 3 == 2) {
+            stockham_pass<T, M, 4, G, NSEQ, SP, NT, INV>(buf, s0, 1, tw);
+            p = 4;
         }
-        for (; p < M; p *= 4) stockham_pass<T, M, 4, G, NSEQ, SP, NT, INV>(buf, s0, p, tw);
+        for (; p < M; p *= 8) stockham_pass<T, M, 8, G, NSEQ, SP, NT, INV>(buf, s0, p, tw);
     }
+}
+
+// cp.async: asynchronous global -> shared copies (no register staging)
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -108,9 +177,11 @@ struct RowCfg {
     // already gives 128+ blocks per component plane
     static constexpr int ROWS = pow2floor(cmax(1, cmin(16, 512 / (NC * M))));   // divides every ny >= 16
     static constexpr int NT = (NC * ROWS * M >= 1024) ? 256 : 128;
-    static constexpr int SP = M + 1;                        // pitch (complex), odd to spread banks
+    static constexpr int SP = padded_len(M) + 2;            // pitch (complex): padded M values + slot for k = M
     static constexpr int NSEQ = NC * ROWS;
-    static constexpr size_t SMEM = (size_t)NSEQ * SP * sizeof(typename CT<T>::t);
+    // twiddles staged in shared memory: length-M FFT table + the M+1 real-FFT factors
+    static constexpr int TWS = 2 * M + 1;
+    static constexpr size_t SMEM = (size_t)(NSEQ * SP + TWS) * sizeof(typename CT<T>::t);
 };
 
 template <typename T, int NY, int NC>
@@ -120,18 +191,29 @@ struct ColCfg {
     // one 32-byte sector per row segment: enough columns per block for full
     // sectors, and as many blocks as possible
     static constexpr int CWE = CWMIN;
-    static constexpr int SP = NY + 1;
+    static constexpr int SP = ((padded_len(NY) + 7) / 16) * 16 + 8;   // pitch = 8 (mod 16) slots
     static constexpr int NSEQ = NC * CWE;
     static constexpr int NT = (NSEQ * NY >= 8192) ? 512 : (NSEQ * NY >= 2048 ? 256 : 128);
-    static constexpr size_t SMEM = (size_t)NSEQ * SP * CSZ;
+    // twiddles in shared memory when they fit next to the data (not for FP64 at 2048)
+    static constexpr bool TW_SMEM = (size_t)(NSEQ * SP + NY) * CSZ <= 225 * 1024;
+    static constexpr size_t SMEM = (size_t)(NSEQ * SP + (TW_SMEM ? NY : 0)) * CSZ;
 };
 
 constexpr int WP_ALIGN = 16;   // spectral row pitch multiple (largest column tile)
 
-// Staging of M+1 spectrum values per sequence in a buffer of pitch SP = M+1
-// (the in-place FFT layout holds M values; the extra slot lives in the pitch pad).
-template <typename C> __device__ __forceinline__ void stage_store(C* buf, int s, int k, int SP, C v) { buf[s * SP + k] = v; }
-template <typename C> __device__ __forceinline__ C stage_load(const C* buf, int s, int k, int SP) { return buf[s * SP + k]; }
+// Per-block mode constants in the storage precision (converted from FP64 once
+// per thread, never per element: the FP64 pipe is narrow).
+template <typename T>
+struct ModeK {
+    T cx, cy, inv_n;
+    int nx, ny;
+    __device__ __forceinline__ explicit ModeK(const Desc<T>& d)
+        : cx(T(d.k.two_pi_over_Lx)), cy(T(d.k.two_pi_over_Ly)), inv_n(T(d.k.inv_n)), nx(d.nx), ny(d.ny) {}
+};
+
+
+// real value x of a real sequence stored as complex pairs z[n] = x[2n] + i x[2n+1]
+__device__ __forceinline__ int ridx(int x) { return 2 * pidx(x >> 1) + (x & 1); }
 
 // ---------------------------------------------------------------------------
 // Functor interface (F):
@@ -150,6 +232,9 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_fwd(const Desc<T>
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     T* rb = reinterpret_cast<T*>(smem_raw);
+    C* tws = buf + Cfg::NSEQ * SP;          // [0, M): FFT table of length M; [M, 2M]: exp(-2 pi i k / NX)
+    for (int t = threadIdx.x; t < Cfg::TWS; t += NT)
+        cp_async<sizeof(C)>(&tws[t], t < M ? &d.tw[M + t] : &d.tw[NX + (t - M)]);
     const int y0 = blockIdx.x * ROWS;
     const typename F::Ctx ctx = F::prep(d);
     constexpr int NRA = F::NR > 0 ? F::NR : 1;
@@ -161,7 +246,7 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_fwd(const Desc<T>
         T v[NC];
         F::pixel(d, ctx, pix, v, &acc[0]);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) rb[(size_t)(c * ROWS + row) * 2 * SP + x] = v[c];
+        for (int c = 0; c < NC; ++c) rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)] = v[c];
     }
     if constexpr (F::NR > 0) {
         double vals[F::NR], tot[F::NR];
@@ -170,16 +255,17 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_fwd(const Desc<T>
         if (reduce_last<F::NR, NT>(vals, d.part, &d.ctrl->counter, gridDim.x, tot) && threadIdx.x == 0)
             F::finalize(d, tot);
     }
+    cp_async_wait_all();
     __syncthreads();
-    fft_smem<T, M, Cfg::NSEQ, SP, NT, false>(buf, d.tw);
+    fft_smem<T, M, Cfg::NSEQ, SP, NT, false>(buf, tws);
     // real-to-complex post-processing: X[k] = Xe[k] + W_N^k Xo[k], k = 0..M
-    const C* twN = d.tw + NX;
+    const C* twN = tws + M;
     const size_t plane = (size_t)d.ny * d.wp;
     for (int t = threadIdx.x; t < Cfg::NSEQ * (M + 1); t += NT) {
         const int s = t / (M + 1), k = t % (M + 1);
         const int c = s / ROWS, row = s % ROWS;
-        C zk = buf[s * SP + (k == M ? 0 : k)];
-        C zm = buf[s * SP + (k == 0 ? 0 : M - k)];
+        C zk = buf[s * SP + pidx(k == M ? 0 : k)];
+        C zm = buf[s * SP + pidx(k == 0 ? 0 : M - k)];
         zm.y = -zm.y;
         C e = C{T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y + zm.y)};
         C o = C{T(0.5) * (zk.y - zm.y), T(-0.5) * (zk.x - zm.x)};
@@ -198,18 +284,22 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const T* rb = reinterpret_cast<const T*>(smem_raw);
+    C* tws = buf + Cfg::NSEQ * SP;
+    for (int t = threadIdx.x; t < Cfg::TWS; t += NT)
+        cp_async<sizeof(C)>(&tws[t], t < M ? &d.tw[M + t] : &d.tw[NX + (t - M)]);
     const int y0 = blockIdx.x * ROWS;
-    const C* twN = d.tw + NX;
+    const C* twN = tws + M;
     const size_t plane = (size_t)d.ny * d.wp;
     // complex-to-real pre-processing: Z[k] = A + i B,
     //   A = X[k] + conj(X[M-k]),  B = (X[k] - conj(X[M-k])) e^{+2 pi i k/N}
     // (imaginary parts of X[0] and X[M] are dropped, as for a real inverse).
-    // stage the half spectrum rows in shared memory first (independent loads), then combine
+    // stage the half spectrum rows in shared memory (asynchronous copies), then combine
     for (int t = threadIdx.x; t < Cfg::NSEQ * (M + 1); t += NT) {
         const int s = t / (M + 1), k = t % (M + 1);
         const int c = s / ROWS, row = s % ROWS;
-        stage_store(buf, s, k, SP, d.S[c * plane + (size_t)(y0 + row) * d.wp + k]);
+        cp_async<sizeof(C)>(&buf[s * SP + pidx(k)], &d.S[c * plane + (size_t)(y0 + row) * d.wp + k]);
     }
+    cp_async_wait_all();
     __syncthreads();
     C z[(Cfg::NSEQ * M + NT - 1) / NT];
 #pragma unroll
@@ -217,7 +307,7 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
         const int t = threadIdx.x + u * NT;
         if ((Cfg::NSEQ * M) % NT == 0 || t < Cfg::NSEQ * M) {
             const int s = t / M, k = t % M;
-            C xk = stage_load<C>(buf, s, k, SP), xm = stage_load<C>(buf, s, M - k, SP);
+            C xk = buf[s * SP + pidx(k)], xm = buf[s * SP + pidx(M - k)];
             if (k == 0) { xk.y = T(0); xm.y = T(0); }
             xm.y = -xm.y;
             C A = cadd(xk, xm);
@@ -229,10 +319,10 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
 #pragma unroll
     for (int u = 0; u < (Cfg::NSEQ * M + NT - 1) / NT; ++u) {
         const int t = threadIdx.x + u * NT;
-        if ((Cfg::NSEQ * M) % NT == 0 || t < Cfg::NSEQ * M) buf[(t / M) * SP + t % M] = z[u];
+        if ((Cfg::NSEQ * M) % NT == 0 || t < Cfg::NSEQ * M) buf[(t / M) * SP + pidx(t % M)] = z[u];
     }
     __syncthreads();
-    fft_smem<T, M, Cfg::NSEQ, SP, NT, true>(buf, d.tw);
+    fft_smem<T, M, Cfg::NSEQ, SP, NT, true>(buf, tws);
     const typename F::Ctx ctx = F::prep(d);
     constexpr int NRA = F::NR > 0 ? F::NR : 1;
     Acc<T> acc[NRA];
@@ -242,7 +332,7 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
         const size_t pix = (size_t)(y0 + row) * NX + x;
         T v[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) v[c] = rb[(size_t)(c * ROWS + row) * 2 * SP + x];
+        for (int c = 0; c < NC; ++c) v[c] = rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)];
         F::pixel(d, ctx, pix, v, &acc[0]);
     }
     if constexpr (F::NR > 0) {
@@ -268,43 +358,35 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
     const int kx0 = blockIdx.x * CW;
     const size_t plane = (size_t)d.ny * d.wp;
     constexpr int TOT = NC * NY * CW;
-    constexpr int LPT = (TOT + NT - 1) / NT;   // elements per thread, loaded before any is stored
-    {
-        C tmp[LPT];
-#pragma unroll
-        for (int u = 0; u < LPT; ++u) {
-            const int t = threadIdx.x + u * NT;
-            if (TOT % NT == 0 || t < TOT) {
-                const int j = t % CW, ky = (t / CW) % NY, c = t / (CW * NY);
-                tmp[u] = d.S[c * plane + (size_t)ky * d.wp + kx0 + j];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < LPT; ++u) {
-            const int t = threadIdx.x + u * NT;
-            if (TOT % NT == 0 || t < TOT) {
-                const int j = t % CW, ky = (t / CW) % NY, c = t / (CW * NY);
-                buf[(c * CW + j) * SP + ky] = tmp[u];
-            }
-        }
+    for (int t = threadIdx.x; t < TOT; t += NT) {
+        const int j = t % CW, ky = (t / CW) % NY, c = t / (CW * NY);
+        cp_async<sizeof(C)>(&buf[(c * CW + j) * SP + pidx(ky)], &d.S[c * plane + (size_t)ky * d.wp + kx0 + j]);
     }
+    const C* tw = d.tw + NY;
+    if constexpr (Cfg::TW_SMEM) {
+        C* tws = buf + Cfg::NSEQ * SP;
+        for (int t = threadIdx.x; t < NY; t += NT) cp_async<sizeof(C)>(&tws[t], &d.tw[NY + t]);
+        tw = tws;
+    }
+    cp_async_wait_all();
     __syncthreads();
-    fft_smem<T, NY, Cfg::NSEQ, SP, NT, false>(buf, d.tw);
+    fft_smem<T, NY, Cfg::NSEQ, SP, NT, false>(buf, tw);
+    const ModeK<T> mk(d);
     for (int t = threadIdx.x; t < CW * NY; t += NT) {
         const int ky = t % NY, j = t / NY;
         C v[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) v[c] = buf[(c * CW + j) * SP + ky];
-        OP::apply(d, kx0 + j, ky, v);
+        for (int c = 0; c < NC; ++c) v[c] = buf[(c * CW + j) * SP + pidx(ky)];
+        OP::apply(mk, kx0 + j, ky, v);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) buf[(c * CW + j) * SP + ky] = v[c];
+        for (int c = 0; c < NC; ++c) buf[(c * CW + j) * SP + pidx(ky)] = v[c];
     }
     __syncthreads();
-    fft_smem<T, NY, Cfg::NSEQ, SP, NT, true>(buf, d.tw);
+    fft_smem<T, NY, Cfg::NSEQ, SP, NT, true>(buf, tw);
 #pragma unroll 4
     for (int t = threadIdx.x; t < TOT; t += NT) {
         const int j = t % CW, ky = (t / CW) % NY, c = t / (CW * NY);
-        d.S[c * plane + (size_t)ky * d.wp + kx0 + j] = buf[(c * CW + j) * SP + ky];
+        d.S[c * plane + (size_t)ky * d.wp + kx0 + j] = buf[(c * CW + j) * SP + pidx(ky)];
     }
 }
 
@@ -316,18 +398,18 @@ __device__ __forceinline__ int signed_k(int k, int n) { return k < n / 2 ? k : k
 // Compatibility projection Gamma(n) (Sec. 3.1.1), zero at q = 0 and on
 // Nyquist modes; scaled by 1/(nx ny).
 template <typename T>
-__device__ __forceinline__ void gamma_apply(const Desc<T>& d, int kx, int ky, typename CT<T>::t (&v)[3]) {
+__device__ __forceinline__ void gamma_apply(const ModeK<T>& m, int kx, int ky, typename CT<T>::t (&v)[3]) {
     using C = typename CT<T>::t;
-    const int M = d.nx / 2;
-    if (kx > M || kx == M || ky == d.ny / 2 || (kx == 0 && ky == 0)) {
+    const int M = m.nx / 2;
+    if (kx >= M || ky == m.ny / 2 || (kx == 0 && ky == 0)) {
         v[0] = C{T(0), T(0)}; v[1] = v[0]; v[2] = v[0];
         return;
     }
-    T qx = T(kx) * T(d.k.two_pi_over_Lx);
-    T qy = T(signed_k(ky, d.ny)) * T(d.k.two_pi_over_Ly);
+    T qx = T(kx) * m.cx;
+    T qy = T(signed_k(ky, m.ny)) * m.cy;
     T inv = T(1) / sqrt(qx * qx + qy * qy);
     T n1 = qx * inv, n2 = qy * inv;
-    T sc = T(d.k.inv_n);
+    T sc = m.inv_n;
     C a = v[0], b = v[1], c = v[2];
     C s1{n1 * a.x + n2 * c.x, n1 * a.y + n2 * c.y};      // zeta n
     C s2{n1 * c.x + n2 * b.x, n1 * c.y + n2 * b.y};
@@ -340,13 +422,12 @@ __device__ __forceinline__ void gamma_apply(const Desc<T>& d, int kx, int ky, ty
 
 // Collocation Laplacian multiplier -|2 pi q|^2 / (nx ny) (Sec. 3.1.2).
 template <typename T>
-__device__ __forceinline__ void lap_apply(const Desc<T>& d, int kx, int ky, typename CT<T>::t (&v)[1]) {
-    T qx = T(kx) * T(d.k.two_pi_over_Lx);
-    T qy = T(signed_k(ky, d.ny)) * T(d.k.two_pi_over_Ly);
-    if (ky == d.ny / 2) qy = T(d.ny / 2) * T(d.k.two_pi_over_Ly);
-    T m = -(qx * qx + qy * qy) * T(d.k.inv_n);
-    v[0].x *= m;
-    v[0].y *= m;
+__device__ __forceinline__ void lap_apply(const ModeK<T>& m, int kx, int ky, typename CT<T>::t (&v)[1]) {
+    T qx = T(kx) * m.cx;
+    T qy = T(signed_k(ky, m.ny)) * m.cy;
+    T f = -(qx * qx + qy * qy) * m.inv_n;
+    v[0].x *= f;
+    v[0].y *= f;
 }
 
 }  // namespace pff

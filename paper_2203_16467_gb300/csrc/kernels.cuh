@@ -35,7 +35,7 @@ __global__ void k_step_begin(const Desc<T>* __restrict__ descs, int np) {
     Ctrl* c = descs[j].ctrl;
     c->nd_a = 0; c->nd_b = 0; c->newton_it = 0; c->needs_fold = 0;
     c->cg_a = 1; c->cg_b = 1; c->cg_it = 0; c->cg_total = 0; c->cg_break = 0;
-    c->pf_a = 1; c->pf_b = 1; c->pf_it = 0; c->pf_break = 0; c->n_active = 0;
+    c->pf_a = 1; c->pf_b = 1; c->pf_it = 0; c->pf_break = 0; c->n_active = 0; c->pf_clamp_iters = 0;
     c->gamma = 1.0; c->rescaled = 0; c->status = 0; c->counter = 0u;
     c->Ff = 0.0;
 }

@@ -20,11 +20,29 @@ namespace pff {
 
 constexpr int PF_STALL = 64;    // FP32 BCCG: iterations without a new smallest ||r|| that end a solve
 
+// Lame constants per unit E in the storage type, read once per block (a per-pixel
+// double-to-float conversion would run on the narrow FP64 pipe).
+template <typename T>
+struct LameC {
+    T lc, mc;
+    __device__ __forceinline__ explicit LameC(const Desc<T>& d) : lc(T(d.k.lam_c)), mc(T(d.k.mu_c)) {}
+    __device__ __forceinline__ void at(const Desc<T>& d, size_t i, T& lam, T& mu) const {
+        T E = d.E[i];
+        lam = lc * E;
+        mu = mc * E;
+    }
+};
 template <typename T>
 __device__ __forceinline__ void lame_at(const Desc<T>& d, size_t i, T& lam, T& mu) {
     T E = d.E[i];
     lam = T(d.k.lam_c) * E;
     mu = T(d.k.mu_c) * E;
+}
+
+// FP64 sign of a*x - kappa*l - b from FP32 operands; kept out of line so that it
+// only runs for the rare residuals within FP32 rounding of zero.
+static __device__ __noinline__ bool resid_positive_fp64(float a, float x, double kappa, float l, float b) {
+    return ((double)a * (double)x - kappa * (double)l - (double)b) > 0.0;
 }
 template <typename T> __device__ __forceinline__ T hdeg(T phi) { return (T(1) - phi) * (T(1) - phi); }
 
@@ -42,10 +60,10 @@ struct NoCtx {};
 template <typename T>
 struct FNewtonIn {   // eps* += theta (rounds > 0), sigma(eps_bar + eps*, phi)
     static constexpr int NR = 0;
-    struct Ctx { T eb[3]; int fold; int split; };
+    struct Ctx { T eb[3]; int fold; int split; LameC<T> lm; };
     __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->nd_a); }
     __device__ static Ctx prep(const Desc<T>& d) {
-        Ctx c;
+        Ctx c{{}, 0, 0, LameC<T>(d)};
         for (int k = 0; k < 3; ++k) c.eb[k] = T(ldd(&d.ctrl->eps_bar[k]));
         c.fold = ldflag(&d.ctrl->newton_it) > 0;
         c.split = d.k.split;
@@ -58,7 +76,7 @@ struct FNewtonIn {   // eps* += theta (rounds > 0), sigma(eps_bar + eps*, phi)
             d.eps[0][i] = e0; d.eps[1][i] = e1; d.eps[2][i] = e2;
         }
         T lam, mu;
-        lame_at(d, i, lam, mu);
+        c.lm.at(d, i, lam, mu);
         stress(c.split, c.eb[0] + e0, c.eb[1] + e1, c.eb[2] + e2, hdeg(d.phi[i]), lam, mu, v);
     }
     __device__ static void finalize(const Desc<T>&, const double*) {}
@@ -70,8 +88,8 @@ struct FColGammaN {   // Newton trio column pass: copies nd_b = nd_a
         if (blockIdx.x == 0 && threadIdx.x == 0) d.ctrl->nd_b = f;
         return f;
     }
-    template <typename T> __device__ static void apply(const Desc<T>& d, int kx, int ky, typename CT<T>::t (&v)[3]) {
-        gamma_apply(d, kx, ky, v);
+    template <typename T> __device__ static void apply(const ModeK<T>& m, int kx, int ky, typename CT<T>::t (&v)[3]) {
+        gamma_apply(m, kx, ky, v);
     }
 };
 
@@ -107,7 +125,7 @@ struct FNewtonOut {   // R = P sigma; CG start r = p = -R, theta = 0; Newton tes
             c->cg_a = 1;
             c->cg_b = 1;
         } else {
-            const bool linear = (k.split != SPECTRAL);
+            const bool linear = (contact_of(k.split) == ISOTROPIC);
             c->cg_target = linear ? target : fmax(target, k.mech_cg_rtol * rn);
             c->rr = R2;
             c->cg_it = 0;
@@ -126,10 +144,10 @@ struct FNewtonOut {   // R = P sigma; CG start r = p = -R, theta = 0; Newton tes
 template <typename T>
 struct FCgIn {
     static constexpr int NR = 1;
-    struct Ctx { T alpha, beta; int upd; T eb[3]; int split; };
+    struct Ctx { T alpha, beta; int upd; T eb[3]; int split; LameC<T> lm; };
     __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->cg_a); }
     __device__ static Ctx prep(const Desc<T>& d) {
-        Ctx c;
+        Ctx c{T(0), T(0), 0, {}, 0, LameC<T>(d)};
         c.upd = ldflag(&d.ctrl->cg_it) > 0;
         c.alpha = T(ldd(&d.ctrl->alpha));
         c.beta = T(ldd(&d.ctrl->beta));
@@ -157,7 +175,7 @@ struct FCgIn {
         }
         wdot(acc[0], r[0], r[1], r[2], r[0], r[1], r[2]);
         T lam, mu;
-        lame_at(d, i, lam, mu);
+        c.lm.at(d, i, lam, mu);
         tangent(c.split, c.eb[0] + d.eps[0][i], c.eb[1] + d.eps[1][i], c.eb[2] + d.eps[2][i],
                 hdeg(d.phi[i]), lam, mu, p[0], p[1], p[2], v);
     }
@@ -181,8 +199,8 @@ struct FColGammaCG {   // CG column pass: copies cg_a = cg_b
         if (blockIdx.x == 0 && threadIdx.x == 0) d.ctrl->cg_a = f;
         return f;
     }
-    template <typename T> __device__ static void apply(const Desc<T>& d, int kx, int ky, typename CT<T>::t (&v)[3]) {
-        gamma_apply(d, kx, ky, v);
+    template <typename T> __device__ static void apply(const ModeK<T>& m, int kx, int ky, typename CT<T>::t (&v)[3]) {
+        gamma_apply(m, kx, ky, v);
     }
 };
 
@@ -252,22 +270,22 @@ struct FColLapDF {   // column pass of the step's lap(phi); clears needs_fold (r
         if (blockIdx.x == 0 && threadIdx.x == 0) d.ctrl->needs_fold = 0;
         return false;
     }
-    template <typename T> __device__ static void apply(const Desc<T>& d, int kx, int ky, typename CT<T>::t (&v)[1]) {
-        lap_apply(d, kx, ky, v);
+    template <typename T> __device__ static void apply(const ModeK<T>& m, int kx, int ky, typename CT<T>::t (&v)[1]) {
+        lap_apply(m, kx, ky, v);
     }
 };
 
 struct FColLapPlain {
     template <typename T> __device__ static bool skip(const Desc<T>&) { return false; }
-    template <typename T> __device__ static void apply(const Desc<T>& d, int kx, int ky, typename CT<T>::t (&v)[1]) {
-        lap_apply(d, kx, ky, v);
+    template <typename T> __device__ static void apply(const ModeK<T>& m, int kx, int ky, typename CT<T>::t (&v)[1]) {
+        lap_apply(m, kx, ky, v);
     }
 };
 
 struct FColGammaPlain {
     template <typename T> __device__ static bool skip(const Desc<T>&) { return false; }
-    template <typename T> __device__ static void apply(const Desc<T>& d, int kx, int ky, typename CT<T>::t (&v)[3]) {
-        gamma_apply(d, kx, ky, v);
+    template <typename T> __device__ static void apply(const ModeK<T>& m, int kx, int ky, typename CT<T>::t (&v)[3]) {
+        gamma_apply(m, kx, ky, v);
     }
 };
 
@@ -331,13 +349,15 @@ struct FCopyOut {
 template <typename T>
 struct FPfInit {
     static constexpr int NR = 2;
-    struct Ctx { double g; int resc; double eb[3]; };
+    struct Ctx { double g; int resc; double eb[3]; double eta_dt; int frozen; };
     __device__ static bool skip(const Desc<T>&) { return false; }
     __device__ static Ctx prep(const Desc<T>& d) {
         Ctx c;
         c.g = ldd(&d.ctrl->gamma);
         c.resc = ldflag(&d.ctrl->rescaled);
         for (int k = 0; k < 3; ++k) c.eb[k] = c.g * ldd(&d.ctrl->eps_bar[k]);
+        c.eta_dt = ldflag(&d.ctrl->use_override) ? ldd(&d.ctrl->eta_dt_override) : d.k.eta_dt;
+        c.frozen = ldflag(&d.ctrl->con_frozen);
         return c;
     }
     __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, Acc<T>* acc) {
@@ -354,9 +374,9 @@ struct FPfInit {
         T ph = d.phi[i];
         double phd = (double)ph;
         double fp = k.fracture == AT1 ? 1.0 : 2.0 * phd;
-        T a = T(k.eta_dt + 2.0 * psi + k.cf2);
+        T a = T(c.eta_dt + 2.0 * psi + k.cf2);
         T b = T(2.0 * (1.0 - phd) * psi - k.c * fp + k.kappa * (double)d.lap[i]);
-        T pcon = (k.irrev == CRACK_SET) ? (ph >= T(k.crack_thr) ? ph : T(0)) : ph;
+        T pcon = c.frozen ? d.aux[i] : ((k.irrev == CRACK_SET) ? (ph >= T(k.crack_thr) ? ph : T(0)) : ph);
         T vcon = pcon - ph;
         T v = T(0) < vcon ? vcon : T(0);
         bool at = (v == vcon);
@@ -420,8 +440,8 @@ struct FPfA1 {   // p = -r + beta p, zero on the active set; input p
 
 struct FColLapPF {
     template <typename T> __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
-    template <typename T> __device__ static void apply(const Desc<T>& d, int kx, int ky, typename CT<T>::t (&v)[1]) {
-        lap_apply(d, kx, ky, v);
+    template <typename T> __device__ static void apply(const ModeK<T>& m, int kx, int ky, typename CT<T>::t (&v)[1]) {
+        lap_apply(m, kx, ky, v);
     }
 };
 
@@ -452,19 +472,21 @@ struct FPfA3 {   // J p; p.Jp, r.p -> alpha = -(r.p)/(p.Jp)
 
 template <typename T>
 struct FPfB1 {   // v = max(v + alpha p, v_con); bound flag; input v
-    static constexpr int NR = 0;
+    static constexpr int NR = 1;
     struct Ctx { T alpha; };
     __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
     __device__ static Ctx prep(const Desc<T>& d) { return Ctx{T(ldd(&d.ctrl->pf_alpha))}; }
-    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[1], Acc<T>*) {
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[1], Acc<T>* acc) {
         T x = d.th[0][i] + c.alpha * d.th[2][i];
         T vc = d.r[2][i];
-        if (x < vc) x = vc;
+        if (x < vc) { x = vc; acc[0].add(T(1)); }
         d.th[0][i] = x;
         d.flags[i] = (uint8_t)(x == vc ? 1 : 0);
         v[0] = x;
     }
-    __device__ static void finalize(const Desc<T>&, const double*) {}
+    __device__ static void finalize(const Desc<T>& d, const double* tot) {
+        if (tot[0] > 0.0) d.ctrl->pf_clamp_iters += 1;   // iterations in which the clamp changed v
+    }
 };
 
 template <typename T>
@@ -477,17 +499,19 @@ struct FPfB3 {   // r = Jv - b, active set {bound and r > 0} (sign decided in FP
         T x = d.th[0][i], a = d.r[0][i], b = d.r[1][i], ro = d.th[1][i];
         T ax = a * x, kl = c.kappa * v[0];
         T rn = ax - kl - b;
-        T mag = fabs(ax) + fabs(kl) + fabs(b);
         uint8_t fl = d.flags[i];
         bool at = fl & 1;
-        bool pos;
-        if constexpr (sizeof(T) == 8) {
-            pos = rn > T(0);
-        } else {
-            // FP32 residual; decide its sign in FP64 from the same FP32 operands when it is
-            // within rounding of zero (otherwise the FP32 sign is already exact)
-            if (fabs(rn) > T(4e-7) * mag) pos = rn > T(0);
-            else pos = ((double)a * (double)x - c.kd * (double)v[0] - (double)b) > 0.0;
+        bool pos = false;
+        if (at) {   // the sign only matters at the bound
+            if constexpr (sizeof(T) == 8) {
+                pos = rn > T(0);
+            } else {
+                // FP32 residual; decide its sign in FP64 from the same FP32 operands when it is
+                // within rounding of zero (otherwise the FP32 sign is already exact)
+                T mag = fabs(ax) + fabs(kl) + fabs(b);
+                if (fabs(rn) > T(4e-7) * mag) pos = rn > T(0);
+                else pos = resid_positive_fp64(a, x, c.kd, v[0], b);
+            }
         }
         bool active = at && pos;
         if (active) rn = T(0);
@@ -528,10 +552,10 @@ struct FPfB3 {   // r = Jv - b, active set {bound and r > 0} (sign decided in FP
 template <typename T>
 struct FPost {
     static constexpr int NR = 5;
-    struct Ctx { T eb[3]; };
+    struct Ctx { T eb[3]; LameC<T> lm; };
     __device__ static bool skip(const Desc<T>&) { return false; }
     __device__ static Ctx prep(const Desc<T>& d) {
-        Ctx c;
+        Ctx c{{}, LameC<T>(d)};
         for (int k = 0; k < 3; ++k) c.eb[k] = T(ldd(&d.ctrl->eps_bar[k]));
         return c;
     }
@@ -540,7 +564,7 @@ struct FPost {
         T ph = d.phi[i] + v;
         d.phi[i] = ph;
         T lam, mu;
-        lame_at(d, i, lam, mu);
+        c.lm.at(d, i, lam, mu);
         T xx = c.eb[0] + d.eps[0][i], yy = c.eb[1] + d.eps[1][i], xy = c.eb[2] + d.eps[2][i];
         T h = hdeg(ph);
         T s[3];
@@ -567,11 +591,32 @@ struct FPost {
         c->C_bar = Cb;
         c->dphi = dphi;
         c->Fe = tot[3] * k.dA;
-        c->incremented = dphi < k.dphi_min;
+        c->incremented = c->post_mode == 0 && dphi < k.dphi_min;
         if (c->incremented)
             for (int q = 0; q < 3; ++q) c->eps_bar[q] = eb[q] + k.d_eps_bar[q];
         c->broken = Cb < k.C_broken;
     }
+};
+
+// aux = phi_con(phi) (the constraint of an alternating-minimisation increment),
+// aux = phi (time-step retry point), phi = aux (retry)
+template <typename T, int MODE>
+struct FAux {
+    static constexpr int NR = 0;
+    using Ctx = NoCtx;
+    __device__ static bool skip(const Desc<T>&) { return false; }
+    __device__ static Ctx prep(const Desc<T>&) { return Ctx{}; }
+    __device__ static void pixel(const Desc<T>& d, const Ctx&, size_t i, Acc<T>*) {
+        if (MODE == 0) {
+            T ph = d.phi[i];
+            d.aux[i] = (d.k.irrev == CRACK_SET) ? (ph >= T(d.k.crack_thr) ? ph : T(0)) : ph;
+        } else if (MODE == 1) {
+            d.aux[i] = d.phi[i];
+        } else {
+            d.phi[i] = d.aux[i];
+        }
+    }
+    __device__ static void finalize(const Desc<T>&, const double*) {}
 };
 
 }  // namespace pff

@@ -22,8 +22,9 @@ lib = ctypes.CDLL(_LIBPATH)
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_NOT_CONVERGED, ERR_BARRIER_TIMEOUT, ERR_CUDA, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 FP64, MIXED = 0, 1
 AT1, AT2 = 1, 2
-ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE = 0, 1, 2
+ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, VOLDEV, SPECTRAL_VOLDEV = 0, 1, 2, 3, 4
 CRACK_SET, DAMAGE = 0, 1
+NEAR_EQUILIBRIUM, ALTERNATING_MIN, TIME_DEPENDENT = 0, 1, 2
 FIELD_STRAIN, FIELD_EPS_STAR, FIELD_STRESS, FIELD_PHI, FIELD_PSI_PLUS, FIELD_DRIVING_FORCE, \
     FIELD_MODULUS, FIELD_ACTIVE, FIELD_UPDATE = range(9)
 _TENSOR_FIELDS = {FIELD_STRAIN, FIELD_EPS_STAR, FIELD_STRESS}
@@ -37,7 +38,9 @@ class Params(ctypes.Structure):
                 ("eta_over_dt", ctypes.c_double), ("F_max", ctypes.c_double), ("thresh", ctypes.c_double),
                 ("dphi_min", ctypes.c_double), ("C_broken", ctypes.c_double),
                 ("crack_set_threshold", ctypes.c_double), ("d_eps_bar", ctypes.c_double * 3),
-                ("compute_energies", ctypes.c_int)]
+                ("compute_energies", ctypes.c_int), ("evolution", ctypes.c_int), ("tol_am", ctypes.c_double),
+                ("am_max_inner", ctypes.c_int), ("dt_min", ctypes.c_double), ("dt_max", ctypes.c_double),
+                ("dphi_max", ctypes.c_double)]
 
 
 class StepReport(ctypes.Structure):
@@ -47,7 +50,8 @@ class StepReport(ctypes.Structure):
                 ("mech_res", ctypes.c_double), ("pf_res", ctypes.c_double),
                 ("rescaled", ctypes.c_int), ("incremented", ctypes.c_int), ("newton_iters", ctypes.c_int),
                 ("mech_cg_iters", ctypes.c_int), ("bccg_iters", ctypes.c_int), ("n_active", ctypes.c_int),
-                ("istar", ctypes.c_int), ("broken", ctypes.c_int), ("status", ctypes.c_int)]
+                ("istar", ctypes.c_int), ("broken", ctypes.c_int), ("status", ctypes.c_int),
+                ("bccg_clamp_iters", ctypes.c_int), ("dt", ctypes.c_double), ("inner_iters", ctypes.c_int)]
 
     def to_dict(self):
         out = {}
@@ -87,6 +91,7 @@ _SIGS = {
     "pff_batch_admit": (ctypes.c_int, [_P, _P, _IP]),
     "pff_batch_release": (ctypes.c_int, [_P, ctypes.c_int]),
     "pff_batch_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(StepReport), _IP]),
+    "pff_batch_set_group_size": (ctypes.c_int, [_P, ctypes.c_int]),
     "pff_kernel_launches": (ctypes.c_ulonglong, []),
     "pff_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "pff_set_graphs": (ctypes.c_int, [ctypes.c_int]),
@@ -321,6 +326,10 @@ def batch_admit(b, h):
     return s.value
 
 
+def batch_set_group_size(b, n):
+    return _check(lib.pff_batch_set_group_size(b, int(n)))
+
+
 def batch_release(b, slot):
     return _check(lib.pff_batch_release(b, slot))
 
@@ -334,7 +343,9 @@ def batch_step(b, max_slots, n_steps=1):
 
 # ---------------------------------------------------------------------------- convenience wrappers
 _MODEL = {"AT1": AT1, "AT2": AT2, "ISOTROPIC": ISOTROPIC, "SPECTRAL": SPECTRAL,
-          "SPECTRAL_STRESSFREE": SPECTRAL_STRESSFREE, "CRACK_SET": CRACK_SET, "DAMAGE": DAMAGE}
+          "SPECTRAL_STRESSFREE": SPECTRAL_STRESSFREE, "VOLDEV": VOLDEV, "SPECTRAL_VOLDEV": SPECTRAL_VOLDEV,
+          "CRACK_SET": CRACK_SET, "DAMAGE": DAMAGE, "NEAR_EQUILIBRIUM": NEAR_EQUILIBRIUM,
+          "ALTERNATING_MIN": ALTERNATING_MIN, "TIME_DEPENDENT": TIME_DEPENDENT}
 
 
 class Problem:

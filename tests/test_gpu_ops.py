@@ -5,7 +5,7 @@ import pytest
 
 from oracle import constitutive as cm
 from oracle import fourier
-from oracle.params import ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE
+from oracle.params import ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, SPECTRAL_VOLDEV, VOLDEV
 from paper_2203_16467_gb300.inputs import gaussian_field
 from tests.helpers import from3, rel_l2, tensor_rel_l2, to3
 
@@ -70,7 +70,7 @@ def _strains(ny, nx, seed):
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
-@pytest.mark.parametrize("split", [ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE])
+@pytest.mark.parametrize("split", [ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, VOLDEV, SPECTRAL_VOLDEV])
 def test_constitutive_parity(pff, prec, split):
     ny, nx = 32, 64
     rng = np.random.default_rng(9)

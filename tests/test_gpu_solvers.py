@@ -5,7 +5,7 @@ import pytest
 from oracle import constitutive as cm
 from oracle import evolution as ev
 from oracle import mechanics, phasefield
-from oracle.params import AT1, AT2, CRACK_SET, DAMAGE, ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, Params
+from oracle.params import AT1, AT2, CRACK_SET, DAMAGE, ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, SPECTRAL_VOLDEV, VOLDEV, Params
 from paper_2203_16467_gb300.inputs import eps_M, gaussian_field, modulus_field
 from tests.helpers import bar3, from3, rel_l2, tensor_rel_l2, to3
 
@@ -36,7 +36,7 @@ def _gpu_problem(pff, E, prec, par):
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
-@pytest.mark.parametrize("split", [ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE])
+@pytest.mark.parametrize("split", [ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, VOLDEV, SPECTRAL_VOLDEV])
 @pytest.mark.parametrize("ny,nx", [(64, 64), (32, 128)])
 def test_mechanics_solve_parity(pff, prec, split, ny, nx):
     E = modulus_field(ny, nx, 8.0, 3)

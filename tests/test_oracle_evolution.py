@@ -74,3 +74,47 @@ def test_short_run_invariants(split, fracture, irr):
             assert rep["gamma"] < 1.0
         if rep["broken"]:
             break
+
+
+def test_alternating_minimisation_increment():
+    # Algorithm 2: the inner loop ends with ||dphi||_1 < Tol_AM, phi respects the increment's
+    # constraint phi_con(phi_{s,0}), and the strain is in equilibrium with the final phase field.
+    from oracle import mechanics
+    ell = 2.0
+    em = eps_M(1.0, 0.2, 1.0, ell)
+    par = Params(fracture=AT1, split=SPECTRAL, irreversibility=DAMAGE, ell=ell,
+                 d_eps_bar=((0.0, 0.0), (0.0, em / 8)), mech_tol=1e-10, pf_tol=1e-10)
+    E = modulus_field(24, 24, 4.0, 7)
+    st = ev.State.initial(E)
+    st.eps_bar = np.array([[0.0, 0.0], [0.0, 0.95 * em]])
+    for _ in range(3):
+        phi0 = st.phi.copy()
+        rep = ev.am_increment(st, par)
+        assert rep["dphi_L1"] < 1e-3
+        assert np.all(st.phi >= pf.phi_con(phi0, par) - 1e-12)
+    assert rep["inner"] >= 1 and st.phi.max() > 0
+    es, info = mechanics.solve(st.eps_star, st.eps_bar, st.phi, E, par)
+    # one more mechanics solve after the last phase-field solve changes the strain only
+    # by the last (small) phase-field update
+    assert np.abs(es - st.eps_star).max() < 0.05 * np.abs(st.eps_bar).max()
+
+
+def test_time_dependent_step_halves_and_recovers_dt():
+    # Algorithm 3: above the elastic limit a full step (dt_max) evolves phi too much,
+    # so dt is halved until ||dphi||_1 < (dphi)_max; easy steps double dt again.
+    ell = 2.0
+    em = eps_M(1.0, 0.2, 1.0, ell)
+    par = Params(fracture=AT1, split=SPECTRAL, irreversibility=DAMAGE, ell=ell,
+                 d_eps_bar=((0.0, 0.0), (0.0, em / 8)), mech_tol=1e-10, pf_tol=1e-10)
+    E = modulus_field(24, 24, 4.0, 7)
+    st = ev.State.initial(E)
+    st.eps_bar = np.array([[0.0, 0.0], [0.0, 1.3 * em]])
+    rep, dt = ev.td_step(st, par, 2.0 ** 16)
+    assert rep["tries"] > 1 and rep["dphi_L1"] < 1.5
+    assert not rep["incremented"]
+    dts = [dt]
+    for _ in range(30):
+        rep, dt = ev.td_step(st, par, dt)
+        dts.append(dt)
+    assert max(dts) > min(dts)   # dt adapts
+    assert np.all(st.phi >= -1e-12)

@@ -4,7 +4,7 @@ import pytest
 
 from oracle import constitutive as cm
 from oracle import fourier, mechanics
-from oracle.params import ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, Params
+from oracle.params import ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, VOLDEV, Params
 
 
 def test_homogeneous_modulus_gives_zero_polarisation():
@@ -57,7 +57,7 @@ def _range_basis(ny, nx):
     return U[:, s > 1e-10 * s[0]]
 
 
-@pytest.mark.parametrize("split", [ISOTROPIC, SPECTRAL])
+@pytest.mark.parametrize("split", [ISOTROPIC, SPECTRAL, VOLDEV])
 def test_newton_cg_matches_dense_direct_solve_8x8(split):
     ny = nx = 8
     rng = np.random.default_rng(21)
