@@ -154,6 +154,8 @@ typedef struct pff_step_report {
     int bccg_clamp_iters;      /* BCCG iterations in which the projection onto v >= v_con changed v */
     double dt;                 /* time-dependent method: the time step for the next step (units of eta/(G_c/ell)) */
     int inner_iters;           /* alternating minimisation: inner iterations; time-dependent: phase-field tries */
+    int bccg_full_iters;       /* BCCG iterations that evaluated J v explicitly (the others used
+                                  r_new = r + alpha J p, exact when the projection changed nothing) */
 } pff_step_report;
 
 typedef struct pff_problem pff_problem;

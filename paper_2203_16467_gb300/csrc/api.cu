@@ -391,8 +391,9 @@ static void chunk_direct(int kind, const Group& g) {
             launch_row_fwd<T>(RF_PF_A, nx, ny, d, np, st);
             launch_col<T>(CO_LAP_PF, nx, ny, wp, d, np, st);
             launch_row_inv<T>(RI_PF_A, nx, ny, d, np, st);
-            launch_row_fwd<T>(RF_PF_B, nx, ny, d, np, st);
-            launch_col<T>(CO_LAP_PF, nx, ny, wp, d, np, st);
+            launch_elem<T>(EL_PF_B, nx, ny, d, np, st);
+            launch_row_fwd<T>(RF_PF_B, nx, ny, d, np, st);          // only when J v is evaluated
+            launch_col<T>(CO_LAP_PF_FULL, nx, ny, wp, d, np, st);   // explicitly this iteration
             launch_row_inv<T>(RI_PF_B, nx, ny, d, np, st);
         }
     }
@@ -550,6 +551,7 @@ static void fill_report(const Ctrl& c, int split, pff_step_report* r) {
     r->bccg_iters = c.pf_it;
     r->n_active = c.n_active;
     r->bccg_clamp_iters = c.pf_clamp_iters;
+    r->bccg_full_iters = c.pf_full_iters;
     r->dt = 0.0;
     r->inner_iters = 0;
     r->istar = c.istar;
@@ -629,7 +631,7 @@ static int am_increment(pff_problem* h, pff_step_report* out) {
     launch_elem<T>(EL_SAVE_CON, h->nx, h->ny, d, 1, h->st);
     if ((rc = set_method_ctrl(h, 1, 0.0, 1, 1))) return rc;
     bool warmed = h->graphs.exec[0] || h->graphs.exec[1];
-    int inner = 0, cg = 0, pf = 0, clamps = 0, status = 0;
+    int inner = 0, cg = 0, pf = 0, clamps = 0, fulls = 0, status = 0;
     double dphi = 0.0;
     do {
         launch_step_begin<T>(d, 1, h->st);
@@ -642,6 +644,7 @@ static int am_increment(pff_problem* h, pff_step_report* out) {
         cg += c.cg_total;
         pf += c.pf_it;
         clamps += c.pf_clamp_iters;
+        fulls += c.pf_full_iters;
         status |= c.status;
         ++inner;
     } while (dphi >= p.tol_am && inner < p.am_max_inner);
@@ -653,6 +656,7 @@ static int am_increment(pff_problem* h, pff_step_report* out) {
         out->mech_cg_iters = cg;
         out->bccg_iters = pf;
         out->bccg_clamp_iters = clamps;
+        out->bccg_full_iters = fulls;
         out->inner_iters = inner;
         out->incremented = 1;
         out->status = status || inner >= p.am_max_inner ? PFF_ERR_NOT_CONVERGED : PFF_OK;
@@ -677,7 +681,7 @@ static int td_step(pff_problem* h, pff_step_report* out) {
     if ((rc = mech_solve_group<T>(g, p.mech_max_cg, p.mech_max_newton, h, warmed))) return rc;
     lap_phi_group<T>(g, false);
     launch_elem<T>(EL_SAVE_PHI, h->nx, h->ny, d, 1, h->st);
-    int tries = 0, pf = 0, clamps = 0, status = 0;
+    int tries = 0, pf = 0, clamps = 0, fulls = 0, status = 0;
     double dphi = 0.0;
     for (;;) {
         if (tries > 0 && (rc = set_method_ctrl(h, 1, p.Gc / p.ell / dt, 0, 1))) return rc;
@@ -687,6 +691,7 @@ static int td_step(pff_problem* h, pff_step_report* out) {
         dphi = c.dphi;
         pf += c.pf_it;
         clamps += c.pf_clamp_iters;
+        fulls += c.pf_full_iters;
         status |= c.status;
         ++tries;
         if (dphi < p.dphi_max || dt <= p.dt_min || tries >= 64) {
@@ -695,6 +700,7 @@ static int td_step(pff_problem* h, pff_step_report* out) {
         }
         dt *= 0.5;
         launch_elem<T>(EL_RESTORE_PHI, h->nx, h->ny, d, 1, h->st);   // retry from phi_n
+        lap_phi_group<T>(g, false);   // the solve's initial residual overwrote nabla^2 phi_n
     }
     Ctrl c = g.h_ctrl[0];
     h->td_dt = dt;
@@ -705,6 +711,7 @@ static int td_step(pff_problem* h, pff_step_report* out) {
         fill_report(c, h->split, out);
         out->bccg_iters = pf;
         out->bccg_clamp_iters = clamps;
+        out->bccg_full_iters = fulls;
         out->inner_iters = tries;
         out->incremented = inc;
         out->dt = dt;
@@ -1102,7 +1109,8 @@ int pff_solve_phase_field(pff_problem* h, pff_step_report* out) {
         for (int it = 0; it <= p.pf_max_iter + CHUNK; it += CHUNK) {
             for (int c = 0; c < CHUNK; ++c) {
                 run_trio<T>(h, RF_PF_A, CO_LAP_PF, RI_PF_A);
-                run_trio<T>(h, RF_PF_B, CO_LAP_PF, RI_PF_B);
+                launch_elem<T>(EL_PF_B, h->nx, h->ny, d, 1, h->st);
+                run_trio<T>(h, RF_PF_B, CO_LAP_PF_FULL, RI_PF_B);
             }
             int r2 = poll<T>(g, false, h);
             if (r2) return r2;

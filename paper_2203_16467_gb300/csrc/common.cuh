@@ -51,6 +51,9 @@ struct Ctrl {
     // phase field (Algorithm 1)
     double pf_rr, pf_rp, pJp, pf_alpha, pf_beta, pf_target, pf_best;
     int pf_a, pf_b, pf_it, pf_break, n_active, pf_best_it, pf_clamp_iters;
+    // residual recurrence: pf_full = this iteration evaluates Jv explicitly
+    int pf_full, pf_force, pf_confirm, pf_since_full, pf_full_iters;
+    double pf_last_full;
     // post-step (Algorithm 4 lines 12-14)
     double rep_eps_bar[3], sig_bar[3], C_bar, dphi, Fe, Ff;
     int incremented, broken;

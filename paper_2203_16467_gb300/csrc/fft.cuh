@@ -274,6 +274,11 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_fwd(const Desc<T>
     }
 }
 
+// Row-inverse functors may provide use_fft(d): when it returns false the inverse FFT
+// is skipped and the epilogue runs on zeros (elementwise work only).
+template <class F, class = void> struct HasUseFft { static constexpr bool value = false; };
+template <class F> struct HasUseFft<F, decltype((void)&F::use_fft, void())> { static constexpr bool value = true; };
+
 template <typename T, int NX, int NC, class F>
 __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>* __restrict__ descs) {
     using Cfg = RowCfg<T, NX, NC>;
@@ -285,9 +290,12 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
     C* buf = reinterpret_cast<C*>(smem_raw);
     const T* rb = reinterpret_cast<const T*>(smem_raw);
     C* tws = buf + Cfg::NSEQ * SP;
+    bool do_fft = true;
+    if constexpr (HasUseFft<F>::value) do_fft = F::use_fft(d);
+    const int y0 = blockIdx.x * ROWS;
+    if (do_fft) {
     for (int t = threadIdx.x; t < Cfg::TWS; t += NT)
         cp_async<sizeof(C)>(&tws[t], t < M ? &d.tw[M + t] : &d.tw[NX + (t - M)]);
-    const int y0 = blockIdx.x * ROWS;
     const C* twN = tws + M;
     const size_t plane = (size_t)d.ny * d.wp;
     // complex-to-real pre-processing: Z[k] = A + i B,
@@ -323,6 +331,11 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
     }
     __syncthreads();
     fft_smem<T, M, Cfg::NSEQ, SP, NT, true>(buf, tws);
+    } else {
+        T* rz = reinterpret_cast<T*>(smem_raw);
+        for (int t = threadIdx.x; t < Cfg::NSEQ * 2 * SP; t += NT) rz[t] = T(0);
+        __syncthreads();
+    }
     const typename F::Ctx ctx = F::prep(d);
     constexpr int NRA = F::NR > 0 ? F::NR : 1;
     Acc<T> acc[NRA];

@@ -28,6 +28,7 @@ void launch_elem(int op, int nx, int ny, const Desc<T>* d, int np, cudaStream_t 
         case EL_SAVE_CON: go_elem<T, FAux<T, 0>>(nx, ny, d, np, st); break;
         case EL_SAVE_PHI: go_elem<T, FAux<T, 1>>(nx, ny, d, np, st); break;
         case EL_RESTORE_PHI: go_elem<T, FAux<T, 2>>(nx, ny, d, np, st); break;
+        case EL_PF_B: go_elem<T, FPfB1<T>>(nx, ny, d, np, st); break;
         default: break;
     }
     if (tm) timing_end(FAM_ELEM * 16 + op, st);

@@ -381,6 +381,7 @@ struct FPfInit {
         T v = T(0) < vcon ? vcon : T(0);
         bool at = (v == vcon);
         T r = -b;
+        d.lap[i] = r;                 // unmasked residual R = J v - b (v = 0)
         bool active = at && (r > T(0));
         if (active) r = T(0);
         d.th[0][i] = v;
@@ -403,6 +404,14 @@ struct FPfInit {
         c->pf_it = 0;
         c->pf_break = 0;
         c->n_active = 0;
+        c->pf_full = 1;
+        c->pf_force = 0;
+        c->pf_confirm = 0;
+        c->pf_since_full = 0;
+        c->pf_full_iters = 0;
+        c->pf_last_full = rn;
+        c->pf_best = rn;
+        c->pf_best_it = 0;
         int done = rn <= target;
         c->pf_a = done;
         c->pf_b = done;
@@ -454,6 +463,7 @@ struct FPfA3 {   // J p; p.Jp, r.p -> alpha = -(r.p)/(p.Jp)
     __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[1], Acc<T>* acc) {
         T p = d.th[2][i];
         T Jp = d.r[0][i] * p - c.kappa * v[0];
+        d.q[0][i] = Jp;
         acc[0].addp(p, Jp);
         acc[1].addp(d.th[1][i], p);
     }
@@ -470,47 +480,90 @@ struct FPfA3 {   // J p; p.Jp, r.p -> alpha = -(r.p)/(p.Jp)
     }
 };
 
+// v = max(v + alpha p, v_con), bound flag (elementwise).  When the projection
+// changed no value, v_new = v + alpha p exactly and the residual follows
+// R_new = R + alpha J p; the explicit J v_new (two FFT passes) is needed only when
+// a value was clamped, every PF_REFRESH iterations, or to confirm convergence.
+constexpr int PF_REFRESH = 32;
+
 template <typename T>
-struct FPfB1 {   // v = max(v + alpha p, v_con); bound flag; input v
+struct FPfB1 {
     static constexpr int NR = 1;
     struct Ctx { T alpha; };
     __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
     __device__ static Ctx prep(const Desc<T>& d) { return Ctx{T(ldd(&d.ctrl->pf_alpha))}; }
-    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[1], Acc<T>* acc) {
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, Acc<T>* acc) {
         T x = d.th[0][i] + c.alpha * d.th[2][i];
         T vc = d.r[2][i];
         if (x < vc) { x = vc; acc[0].add(T(1)); }
         d.th[0][i] = x;
         d.flags[i] = (uint8_t)(x == vc ? 1 : 0);
-        v[0] = x;
     }
     __device__ static void finalize(const Desc<T>& d, const double* tot) {
-        if (tot[0] > 0.0) d.ctrl->pf_clamp_iters += 1;   // iterations in which the clamp changed v
+        Ctrl* c = d.ctrl;
+        const bool clamped = tot[0] > 0.0;
+        if (clamped) c->pf_clamp_iters += 1;   // iterations in which the clamp changed v
+        c->pf_full = clamped || c->pf_force || c->pf_since_full + 1 >= PF_REFRESH;
+        c->pf_confirm = c->pf_force;
+        c->pf_force = 0;
     }
 };
 
 template <typename T>
-struct FPfB3 {   // r = Jv - b, active set {bound and r > 0} (sign decided in FP64), beta, convergence
+struct FPfVIn {   // input v for the explicit J v (only when pf_full)
+    static constexpr int NR = 0;
+    using Ctx = NoCtx;
+    __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a) || !ldflag(&d.ctrl->pf_full); }
+    __device__ static Ctx prep(const Desc<T>&) { return Ctx{}; }
+    __device__ static void pixel(const Desc<T>& d, const Ctx&, size_t i, T (&v)[1], Acc<T>*) { v[0] = d.th[0][i]; }
+    __device__ static void finalize(const Desc<T>&, const double*) {}
+};
+
+struct FColLapPFFull {
+    template <typename T> __device__ static bool skip(const Desc<T>& d) {
+        return ldflag(&d.ctrl->pf_a) || !ldflag(&d.ctrl->pf_full);
+    }
+    template <typename T> __device__ static void apply(const ModeK<T>& m, int kx, int ky, typename CT<T>::t (&v)[1]) {
+        lap_apply(m, kx, ky, v);
+    }
+};
+
+template <typename T>
+struct FPfB3 {   // R = Jv - b (explicit or by recurrence), active set {bound and R > 0}, beta, convergence
     static constexpr int NR = 3;
-    struct Ctx { T kappa; double kd; };
+    struct Ctx { T kappa; double kd; T alpha; int full; };
     __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
-    __device__ static Ctx prep(const Desc<T>& d) { return Ctx{T(d.k.kappa), d.k.kappa}; }
+    __device__ static bool use_fft(const Desc<T>& d) { return ldflag(&d.ctrl->pf_full); }
+    __device__ static Ctx prep(const Desc<T>& d) {
+        return Ctx{T(d.k.kappa), d.k.kappa, T(ldd(&d.ctrl->pf_alpha)), ldflag(&d.ctrl->pf_full)};
+    }
     __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[1], Acc<T>* acc) {
-        T x = d.th[0][i], a = d.r[0][i], b = d.r[1][i], ro = d.th[1][i];
-        T ax = a * x, kl = c.kappa * v[0];
-        T rn = ax - kl - b;
+        T ro = d.th[1][i];
+        T rn, x = T(0), a = T(0), b = T(0), kl = T(0);
+        if (c.full) {
+            x = d.th[0][i];
+            a = d.r[0][i];
+            b = d.r[1][i];
+            kl = c.kappa * v[0];
+            rn = a * x - kl - b;
+        } else {
+            rn = d.lap[i] + c.alpha * d.q[0][i];
+        }
+        d.lap[i] = rn;
         uint8_t fl = d.flags[i];
         bool at = fl & 1;
         bool pos = false;
         if (at) {   // the sign only matters at the bound
             if constexpr (sizeof(T) == 8) {
                 pos = rn > T(0);
-            } else {
-                // FP32 residual; decide its sign in FP64 from the same FP32 operands when it is
-                // within rounding of zero (otherwise the FP32 sign is already exact)
-                T mag = fabs(ax) + fabs(kl) + fabs(b);
+            } else if (c.full) {
+                // FP32 residual; decide its sign in FP64 from the same FP32 operands when it
+                // is within rounding of zero (otherwise the FP32 sign is already exact)
+                T mag = fabs(a * x) + fabs(kl) + fabs(b);
                 if (fabs(rn) > T(4e-7) * mag) pos = rn > T(0);
                 else pos = resid_positive_fp64(a, x, c.kd, v[0], b);
+            } else {
+                pos = rn > T(0);
             }
         }
         bool active = at && pos;
@@ -529,17 +582,25 @@ struct FPfB3 {   // r = Jv - b, active set {bound and r > 0} (sign decided in FP
         c->pf_rr = rr;
         c->pf_it += 1;
         c->n_active = (int)tot[2];
-        // r = Jv - b is recomputed explicitly each iteration, so in FP32 its norm
-        // stalls at the rounding level of that evaluation; an FP32 solve whose
-        // residual has not reached a new minimum for PF_STALL iterations has
-        // converged as far as the arithmetic allows.  FP64 solves use the plain
-        // tolerance test of Algorithm 1.
         double rn = sqrt(rr);
-        if (c->pf_it == 1 || rn < c->pf_best) { c->pf_best = rn; c->pf_best_it = c->pf_it; }
+        bool conv = false;
+        if (c->pf_full) {
+            c->pf_full_iters += 1;
+            c->pf_since_full = 0;
+            conv = rn <= c->pf_target;
+            // FP32: a confirming evaluation that improved little on the previous explicit
+            // residual has reached the rounding level of Jv - b
+            if (!conv && sizeof(T) == 4 && c->pf_confirm && rn >= 0.5 * c->pf_last_full) conv = true;
+            c->pf_last_full = rn;
+        } else {
+            c->pf_since_full += 1;
+            if (rn <= c->pf_target) c->pf_force = 1;   // confirm with an explicit residual first
+        }
+        // FP32 safety net: no new smallest explicit residual for PF_STALL iterations
+        if (c->pf_full && rn < c->pf_best) { c->pf_best = rn; c->pf_best_it = c->pf_it; }
         bool stalled = sizeof(T) == 4 && c->pf_it - c->pf_best_it >= PF_STALL;
-        bool conv = rn <= c->pf_target || stalled;
-        if (conv || c->pf_it >= d.k.max_pf || c->pf_break) {
-            if (!conv && !c->pf_break) c->status |= 2;
+        if (conv || stalled || c->pf_it >= d.k.max_pf || c->pf_break) {
+            if (!conv && !stalled && !c->pf_break) c->status |= 2;
             c->pf_b = 1;
         } else {
             c->pf_b = 0;

@@ -51,7 +51,8 @@ class StepReport(ctypes.Structure):
                 ("rescaled", ctypes.c_int), ("incremented", ctypes.c_int), ("newton_iters", ctypes.c_int),
                 ("mech_cg_iters", ctypes.c_int), ("bccg_iters", ctypes.c_int), ("n_active", ctypes.c_int),
                 ("istar", ctypes.c_int), ("broken", ctypes.c_int), ("status", ctypes.c_int),
-                ("bccg_clamp_iters", ctypes.c_int), ("dt", ctypes.c_double), ("inner_iters", ctypes.c_int)]
+                ("bccg_clamp_iters", ctypes.c_int), ("dt", ctypes.c_double), ("inner_iters", ctypes.c_int),
+                ("bccg_full_iters", ctypes.c_int)]
 
     def to_dict(self):
         out = {}
