@@ -270,9 +270,24 @@ int pff_apply_laplacian_noalloc(int nx, int ny, double dx, const double* in_dev,
 unsigned long long pff_kernel_launches(void);
 
 /* Replay the fixed per-iteration launch sequences of the CG and BCCG loops
- * from captured CUDA graphs (default on).  Graphs are used only on problems or
- * batches created with a non-NULL stream and while kernel timing is off. */
+ * from captured CUDA graphs (default on = 1: plain graphs, in which the
+ * explicit J v - b chain of a BCCG iteration that does not need it launches and
+ * returns at once).  on = 2 puts that chain in a conditional graph node that a
+ * one-thread kernel opens only in iterations that need it (measured slower on
+ * GB300 than the returning kernels); 0 launches every kernel directly.  Results do not depend on the
+ * setting.  Graphs are used only on problems or batches created with a
+ * non-NULL stream and while kernel timing is off.  Synchronises the device. */
 int pff_set_graphs(int on);
+
+/* Launch the FP32 FFT-pass and elementwise kernels with programmatic stream
+ * serialization (default on): each kernel's blocks may be scheduled while its
+ * predecessor on the stream is still running and wait on the device for its
+ * completion before touching any field, which hides the launch latency between
+ * the short kernels of one solver iteration.  Applies to direct launches only
+ * (graph replays keep plain edges, which measured faster).  Results do not
+ * depend on the setting.  Off while kernel timing is on.  Synchronises the
+ * device.  No counterpart in the paper (an execution detail of this library). */
+int pff_set_pdl(int on);
 
 /* Kernel timing for benchmarks.  When enabled, every launch of the library is
  * bracketed by CUDA events on its own stream; pff_timing_read returns the

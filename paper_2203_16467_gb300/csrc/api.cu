@@ -25,7 +25,7 @@
 namespace pff {
 
 static std::atomic<unsigned long long> g_launches{0};
-static thread_local bool t_capturing = false;
+static thread_local bool t_capturing = false;   // this thread is capturing a graph
 void count_launch() {
     if (!t_capturing) g_launches.fetch_add(1, std::memory_order_relaxed);
 }
@@ -42,6 +42,13 @@ struct TimingState {
 static TimingState g_tm;
 static thread_local std::map<int, cudaEvent_t> t_open;   // begin events of this host thread
 bool timing_on() { return g_tm.on; }
+
+// programmatic dependent launch of the operator kernels (off while timing: the
+// per-kernel events need each kernel to start after its predecessor completed)
+static std::atomic<bool> g_pdl{true};
+// (inside captured graphs programmatic edges measured slower than plain kernel
+// edges, so only direct launches use it)
+bool pdl_on() { return g_pdl.load(std::memory_order_relaxed) && !g_tm.on && !t_capturing; }
 static cudaEvent_t tm_event() {
     if (!g_tm.pool.empty()) { cudaEvent_t e = g_tm.pool.back(); g_tm.pool.pop_back(); return e; }
     cudaEvent_t e;
@@ -184,13 +191,16 @@ static bool valid_n(int n) { return n >= 16 && n <= 2048 && (n & (n - 1)) == 0; 
 struct GraphCache {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     int nodes[2] = {0, 0};
+    bool failed[2] = {false, false};   // capture or instantiation failed: launch directly
     const void* desc = nullptr;
     int np = 0;
+    int cond = -1;                     // conditional-node setting the graphs were captured with
     void reset() {
         for (int k = 0; k < 2; ++k) {
             if (exec[k]) cudaGraphExecDestroy(exec[k]);
             exec[k] = nullptr;
             nodes[k] = 0;
+            failed[k] = false;
         }
     }
 };
@@ -376,6 +386,7 @@ struct Group {
 
 static const int CHUNK = 8;
 static bool g_graphs_enabled = true;
+static bool g_cond_nodes = false;  // BCCG explicit-residual chain in conditional graph nodes
 
 template <typename T>
 static void chunk_direct(int kind, const Group& g) {
@@ -399,6 +410,82 @@ static void chunk_direct(int kind, const Group& g) {
     }
 }
 
+// Capture of a BCCG chunk in which the explicit J v - b chain of each iteration
+// sits in a conditional (IF) graph node: a one-thread kernel sets the condition
+// from the problems' pf_full flags, so iterations that take the residual by
+// recurrence launch no kernels for the chain.
+static cudaStream_t side_stream() {
+    static thread_local std::map<int, cudaStream_t> side;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto it = side.find(dev);
+    if (it != side.end()) return it->second;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    side[dev] = s;
+    return s;
+}
+
+template <typename T>
+static cudaError_t capture_pf_chunk(const Group& g, cudaGraph_t* out, int* kernels) {
+    const Desc<T>* d = (const Desc<T>*)g.d_desc;
+    const int nx = g.nx, ny = g.ny, wp = g.wp, np = g.np;
+    cudaStream_t st = g.st, sd = side_stream();
+    if (!sd) return cudaErrorNotSupported;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, graph, 0, 0)) != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+    if ((e = cudaStreamBeginCaptureToGraph(st, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return e;
+    }
+    int nk = 0;
+    for (int c = 0; c < CHUNK && e == cudaSuccess; ++c) {
+        launch_row_fwd<T>(RF_PF_A, nx, ny, d, np, st);
+        launch_col<T>(CO_LAP_PF, nx, ny, wp, d, np, st);
+        launch_row_inv<T>(RI_PF_A, nx, ny, d, np, st);
+        launch_elem<T>(EL_PF_B, nx, ny, d, np, st);
+        launch_pf_cond<T>(d, np, h, st);
+        nk += 5;
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        if ((e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd)) != cudaSuccess) break;
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        if ((e = cudaGraphAddNode(&node, graph, deps, nullptr, nd, &cp)) != cudaSuccess) break;
+        if ((e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+            cudaSuccess)
+            break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(sd, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess)
+            break;
+        launch_row_fwd<T>(RF_PF_B, nx, ny, d, np, sd);
+        launch_col<T>(CO_LAP_PF_FULL, nx, ny, wp, d, np, sd);
+        launch_row_inv<T>(RI_PF_B, nx, ny, d, np, sd);
+        cudaGraph_t body_out = nullptr;
+        if ((e = cudaStreamEndCapture(sd, &body_out)) != cudaSuccess) break;
+    }
+    cudaGraph_t done = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(st, &done);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return e;
+    }
+    *out = graph;
+    *kernels = nk;
+    return cudaSuccess;
+}
+
 // One chunk of iterations: replayed from a captured graph when the group has a
 // graph cache and a non-default stream, and timing is off; launched directly otherwise.
 template <typename T>
@@ -415,30 +502,45 @@ static void run_chunk(int kind, Group& g, bool& warmed) {
         warmed = true;   // attributes (shared-memory opt-in) are set by the first direct chunk
         return;
     }
-    if (gc->desc != g.d_desc || gc->np != g.np) {
+    if (gc->desc != g.d_desc || gc->np != g.np || gc->cond != (int)g_cond_nodes) {
         gc->reset();
         gc->desc = g.d_desc;
         gc->np = g.np;
+        gc->cond = (int)g_cond_nodes;
+    }
+    if (gc->failed[kind]) {
+        chunk_direct<T>(kind, g);
+        return;
     }
     if (!gc->exec[kind]) {
         cudaGraph_t graph = nullptr;
+        int nk = 0;
+        cudaError_t e = cudaSuccess;
         t_capturing = true;
-        cudaError_t e = cudaStreamBeginCapture(g.st, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            chunk_direct<T>(kind, g);
-            e = cudaStreamEndCapture(g.st, &graph);
+        if (kind == 1 && g_cond_nodes) {
+            e = capture_pf_chunk<T>(g, &graph, &nk);
+        } else {
+            e = cudaStreamBeginCapture(g.st, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                chunk_direct<T>(kind, g);
+                e = cudaStreamEndCapture(g.st, &graph);
+            }
+            if (graph) {
+                size_t n = 0;
+                cudaGraphGetNodes(graph, nullptr, &n);
+                nk = (int)n;
+            }
         }
         t_capturing = false;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&gc->exec[kind], graph, 0);
         if (graph) {
-            size_t n = 0;
-            cudaGraphGetNodes(graph, nullptr, &n);
-            gc->nodes[kind] = (int)n;
+            gc->nodes[kind] = nk;
             cudaGraphDestroy(graph);
         }
         if (e != cudaSuccess) {
             cudaGetLastError();
             gc->exec[kind] = nullptr;
+            gc->failed[kind] = true;
             chunk_direct<T>(kind, g);
             return;
         }
@@ -1361,7 +1463,15 @@ int pff_batch_step(pff_batch* b, int n_steps, pff_step_report* reports, int* ste
 unsigned long long pff_kernel_launches(void) { return g_launches.load(); }
 
 int pff_set_graphs(int on) {
+    cudaDeviceSynchronize();
     g_graphs_enabled = on != 0;
+    g_cond_nodes = on == 2;
+    return PFF_OK;
+}
+
+int pff_set_pdl(int on) {
+    cudaDeviceSynchronize();
+    g_pdl.store(on != 0);
     return PFF_OK;
 }
 

@@ -53,6 +53,7 @@ struct Ctrl {
     int pf_a, pf_b, pf_it, pf_break, n_active, pf_best_it, pf_clamp_iters;
     // residual recurrence: pf_full = this iteration evaluates Jv explicitly
     int pf_full, pf_force, pf_confirm, pf_since_full, pf_full_iters;
+    int pf_rsel;            // the BCCG residual r lives in th[1] (0) or q[1] (1)
     double pf_last_full;
     // post-step (Algorithm 4 lines 12-14)
     double rep_eps_bar[3], sig_bar[3], C_bar, dphi, Fe, Ff;
@@ -111,6 +112,17 @@ struct Desc {
 };
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel's blocks may be scheduled while the
+// previous kernel of the stream is still running; they do only work on
+// immutable data (descriptor, twiddle tables) before pdl_wait(), which returns
+// once the previous kernel has completed and its writes are visible.  Each
+// kernel then lets the next one be scheduled.  Both are no-ops for launches
+// without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() { pdl_wait(); pdl_release(); }
+
+// ---------------------------------------------------------------------------
 // flag access (bypass L1: flags are written by other kernels / blocks)
 __device__ __forceinline__ int ldflag(const int* p) { return __ldcg(p); }
 __device__ __forceinline__ double ldd(const double* p) { return __ldcg(p); }
@@ -118,8 +130,22 @@ __device__ __forceinline__ double ldd(const double* p) { return __ldcg(p); }
 // ---------------------------------------------------------------------------
 // Per-thread accumulation.  FP64 problems accumulate in double.  FP32 problems
 // accumulate products exactly split (fmaf) and summed with Knuth's two-sum in
-// a float pair, and switch to double at the warp level: the pointwise work
-// stays on the FP32 pipe while the sums keep FP64-level accuracy.
+// a float pair, and reduce across the grid in double-float arithmetic
+// (reduce_grid): the work stays on the FP32 pipe while the sums keep close to
+// FP64 accuracy.
+// Functors whose per-pixel work splits into load() (returning an In record) and
+// pixel(..., const In&, ...) let a kernel issue the loads of all of a thread's
+// pixels before the first store, so that they are in flight together.
+template <class F, class = void> struct HasIn { static constexpr bool value = false; };
+template <class F> struct HasIn<F, decltype((void)sizeof(typename F::In), void())> { static constexpr bool value = true; };
+
+template <class F, class D, class X, class... A>
+__device__ __forceinline__ void pixel_one(const D& d, const X& c, size_t i, A&&... a) {
+    if constexpr (HasIn<F>::value) F::pixel(d, c, i, F::load(d, c, i), a...);
+    else F::pixel(d, c, i, a...);
+}
+
+struct DF { float hi, lo; };   // double-float value hi + lo (see reduce_grid)
 template <typename T> struct Acc;
 template <> struct Acc<double> {
     double s = 0.0;
@@ -136,42 +162,94 @@ template <> struct Acc<float> {
         s = t;
     }
     __device__ __forceinline__ void addp(float a, float b) {
-        float pr = a * b;
+        float pr = __fmul_rn(a, b);   // not contracted into the two-sum below
         float e = fmaf(a, b, -pr);
         add(pr);
         c += e;
     }
     __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+    __device__ __forceinline__ DF df() const {   // normalised double-float pair
+        float h = s + c;
+        float z = h - s;
+        return DF{h, (s - (h - z)) + (c - z)};
+    }
 };
 
-// Block reduction of NR doubles into part[blockIdx.x*NR + k]; the last block
-// of the problem (by an atomic ticket) sums all partials in a fixed order and
-// returns true with the totals in tot (valid in thread 0).  Deterministic: the
-// summation tree depends only on the grid shape.
-template <int NR, int NT>
-__device__ __forceinline__ bool reduce_last(double (&v)[NR], double* part, unsigned* counter, int nblocks,
+// Grid reductions.  Each block reduces its threads' values (warp shuffles, then
+// one shuffle tree over the warp totals in warp 0) into part[blockIdx.x*NR + k];
+// the last block of the problem (by an atomic ticket) sums all partials in a
+// fixed order and returns true with the totals in tot (valid in thread 0).
+// Deterministic: the summation tree depends only on the grid shape.
+//
+// FP32 problems reduce in double-float arithmetic (a value is an unevaluated
+// sum hi + lo of two floats, added with Knuth's two-sum), so that every level
+// stays on the FP32 pipe with about 44 significant bits and only the final
+// totals are converted to double; their partials are stored as float2.
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    float s = a.hi + b.hi;
+    float z = s - a.hi;
+    float e = (a.hi - (s - z)) + (b.hi - z);
+    e += a.lo + b.lo;
+    float h = s + e;
+    return DF{h, e - (h - s)};
+}
+
+template <typename V> struct RedOps;
+template <> struct RedOps<double> {
+    __device__ static double zero() { return 0.0; }
+    __device__ static double add(double a, double b) { return a + b; }
+    __device__ static double shfl(double a, int o) { return __shfl_down_sync(0xffffffffu, a, o); }
+    __device__ static void store(double* part, size_t j, double v) { __stcg(part + j, v); }
+    __device__ static double load(const double* part, size_t j) { return __ldcg(part + j); }
+    __device__ static double total(double v) { return v; }
+};
+template <> struct RedOps<DF> {
+    __device__ static DF zero() { return DF{0.f, 0.f}; }
+    __device__ static DF add(DF a, DF b) { return df_add(a, b); }
+    __device__ static DF shfl(DF a, int o) {
+        return DF{__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+    }
+    __device__ static void store(double* part, size_t j, DF v) {
+        __stcg(reinterpret_cast<float2*>(part) + j, make_float2(v.hi, v.lo));
+    }
+    __device__ static DF load(const double* part, size_t j) {
+        float2 y = __ldcg(reinterpret_cast<const float2*>(part) + j);
+        return DF{y.x, y.y};
+    }
+    __device__ static double total(DF v) { return (double)v.hi + (double)v.lo; }
+};
+
+template <int NR, int NT, typename V>
+__device__ __forceinline__ bool reduce_grid(V (&v)[NR], double* part, unsigned* counter, int nblocks,
                                             double (&tot)[NR]) {
-    __shared__ double sh[NR][NT / 32];
+    using O = RedOps<V>;
+    constexpr int NW = NT / 32;
+    __shared__ V sh[NR][NW];
     __shared__ int s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
-        double x = v[k];
+        V x = v[k];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        for (int o = 16; o > 0; o >>= 1) x = O::add(x, O::shfl(x, o));
         if (lane == 0) sh[k][warp] = x;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
+        V x[NR];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            double x = 0.0;
-            for (int w = 0; w < NT / 32; ++w) x += sh[k][w];
-            __stcg(&part[(size_t)blockIdx.x * NR + k], x);
+        for (int k = 0; k < NR; ++k) x[k] = lane < NW ? sh[k][lane] : O::zero();
+#pragma unroll
+        for (int o = NW / 2; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < NR; ++k) x[k] = O::add(x[k], O::shfl(x[k], o));
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < NR; ++k) O::store(part, (size_t)blockIdx.x * NR + k, x[k]);
+            __threadfence();
+            unsigned t = atomicAdd(counter, 1u);
+            s_last = (t == (unsigned)(nblocks - 1));
         }
-        __threadfence();
-        unsigned t = atomicAdd(counter, 1u);
-        s_last = (t == (unsigned)(nblocks - 1));
     }
     __syncthreads();
     if (!s_last) return false;
@@ -179,23 +257,45 @@ __device__ __forceinline__ bool reduce_last(double (&v)[NR], double* part, unsig
     // fixed-order sum of the partials: thread t takes blocks t, t+NT, ... in order
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
-        double x = 0.0;
-        for (int b = threadIdx.x; b < nblocks; b += NT) x += __ldcg(&part[(size_t)b * NR + k]);
+        V x = O::zero();
+        for (int b = threadIdx.x; b < nblocks; b += NT) x = O::add(x, O::load(part, (size_t)b * NR + k));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        for (int o = 16; o > 0; o >>= 1) x = O::add(x, O::shfl(x, o));
         if (lane == 0) sh[k][warp] = x;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
+        V x[NR];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            double x = 0.0;
-            for (int w = 0; w < NT / 32; ++w) x += sh[k][w];
-            tot[k] = x;
+        for (int k = 0; k < NR; ++k) x[k] = lane < NW ? sh[k][lane] : O::zero();
+#pragma unroll
+        for (int o = NW / 2; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < NR; ++k) x[k] = O::add(x[k], O::shfl(x[k], o));
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < NR; ++k) tot[k] = O::total(x[k]);
+            *counter = 0u;
         }
-        *counter = 0u;
     }
     return true;
+}
+
+// Block + grid reduction of the per-thread accumulators.
+template <int NR, int NT, typename T>
+__device__ __forceinline__ bool reduce_acc(const Acc<T>* acc, double* part, unsigned* counter, int nblocks,
+                                           double (&tot)[NR]) {
+    if constexpr (sizeof(T) == 4) {
+        DF v[NR];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) v[k] = acc[k].df();
+        return reduce_grid<NR, NT>(v, part, counter, nblocks, tot);
+    } else {
+        double v[NR];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) v[k] = acc[k].get();
+        return reduce_grid<NR, NT>(v, part, counter, nblocks, tot);
+    }
 }
 
 // ---------------------------------------------------------------------------

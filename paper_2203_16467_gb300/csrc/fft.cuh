@@ -222,37 +222,62 @@ __device__ __forceinline__ int ridx(int x) { return 2 * pidx(x >> 1) + (x & 1); 
 //   static bool skip(const Desc<T>&);             // whole-problem early exit
 //   static void pixel(const Desc<T>&, const Ctx&, size_t i, T (&v)[NC], Acc<T> (&acc)[NR]);
 //   static void finalize(const Desc<T>&, const double (&tot)[NR]);   // one thread
+template <class F, bool TWO> struct InOf { struct type {}; };
+template <class F> struct InOf<F, true> { using type = typename F::In; };
+
 template <typename T, int NX, int NC, class F>
 __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_fwd(const Desc<T>* __restrict__ descs) {
     using Cfg = RowCfg<T, NX, NC>;
     using C = typename CT<T>::t;
     constexpr int M = Cfg::M, SP = Cfg::SP, ROWS = Cfg::ROWS, NT = Cfg::NT;
     const Desc<T>& d = descs[blockIdx.y];
-    if (F::skip(d)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     T* rb = reinterpret_cast<T*>(smem_raw);
     C* tws = buf + Cfg::NSEQ * SP;          // [0, M): FFT table of length M; [M, 2M]: exp(-2 pi i k / NX)
     for (int t = threadIdx.x; t < Cfg::TWS; t += NT)
         cp_async<sizeof(C)>(&tws[t], t < M ? &d.tw[M + t] : &d.tw[NX + (t - M)]);
+    pdl_enter();
+    const typename F::Ctx ctx = F::prep(d);   // issued with the skip test
+    if (F::skip(d)) { cp_async_wait_all(); return; }
     const int y0 = blockIdx.x * ROWS;
-    const typename F::Ctx ctx = F::prep(d);
     constexpr int NRA = F::NR > 0 ? F::NR : 1;
     Acc<T> acc[NRA];
-#pragma unroll 4
-    for (int t = threadIdx.x; t < ROWS * NX; t += NT) {
-        const int row = t / NX, x = t % NX;
-        const size_t pix = (size_t)(y0 + row) * NX + x;
-        T v[NC];
-        F::pixel(d, ctx, pix, v, &acc[0]);
+    if constexpr (HasIn<F>::value && (ROWS * NX) % NT == 0) {
+        constexpr int PPT = ROWS * NX / NT;
+        constexpr int G = PPT < 4 ? PPT : 4;   // pixels whose loads are in flight together
 #pragma unroll
-        for (int c = 0; c < NC; ++c) rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)] = v[c];
+        for (int j0 = 0; j0 < PPT; j0 += G) {
+            typename F::In in[G];
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                const int t = threadIdx.x + (j0 + j) * NT;
+                in[j] = F::load(d, ctx, (size_t)(y0 + t / NX) * NX + t % NX);
+            }
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                const int t = threadIdx.x + (j0 + j) * NT;
+                const int row = t / NX, x = t % NX;
+                T v[NC];
+                F::pixel(d, ctx, (size_t)(y0 + row) * NX + x, in[j], v, &acc[0]);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)] = v[c];
+            }
+        }
+    } else {
+#pragma unroll 4
+        for (int t = threadIdx.x; t < ROWS * NX; t += NT) {
+            const int row = t / NX, x = t % NX;
+            const size_t pix = (size_t)(y0 + row) * NX + x;
+            T v[NC];
+            pixel_one<F>(d, ctx, pix, v, &acc[0]);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)] = v[c];
+        }
     }
     if constexpr (F::NR > 0) {
-        double vals[F::NR], tot[F::NR];
-#pragma unroll
-        for (int k = 0; k < F::NR; ++k) vals[k] = acc[k].get();
-        if (reduce_last<F::NR, NT>(vals, d.part, &d.ctrl->counter, gridDim.x, tot) && threadIdx.x == 0)
+        double tot[F::NR];
+        if (reduce_acc<F::NR, NT>(acc, d.part, &d.ctrl->counter, gridDim.x, tot) && threadIdx.x == 0)
             F::finalize(d, tot);
     }
     cp_async_wait_all();
@@ -274,28 +299,34 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_fwd(const Desc<T>
     }
 }
 
-// Row-inverse functors may provide use_fft(d): when it returns false the inverse FFT
-// is skipped and the epilogue runs on zeros (elementwise work only).
-template <class F, class = void> struct HasUseFft { static constexpr bool value = false; };
-template <class F> struct HasUseFft<F, decltype((void)&F::use_fft, void())> { static constexpr bool value = true; };
-
 template <typename T, int NX, int NC, class F>
 __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>* __restrict__ descs) {
     using Cfg = RowCfg<T, NX, NC>;
     using C = typename CT<T>::t;
     constexpr int M = Cfg::M, SP = Cfg::SP, ROWS = Cfg::ROWS, NT = Cfg::NT;
     const Desc<T>& d = descs[blockIdx.y];
-    if (F::skip(d)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const T* rb = reinterpret_cast<const T*>(smem_raw);
     C* tws = buf + Cfg::NSEQ * SP;
-    bool do_fft = true;
-    if constexpr (HasUseFft<F>::value) do_fft = F::use_fft(d);
     const int y0 = blockIdx.x * ROWS;
-    if (do_fft) {
     for (int t = threadIdx.x; t < Cfg::TWS; t += NT)
         cp_async<sizeof(C)>(&tws[t], t < M ? &d.tw[M + t] : &d.tw[NX + (t - M)]);
+    pdl_enter();
+    const typename F::Ctx ctx = F::prep(d);   // issued with the skip test
+    if (F::skip(d)) { cp_async_wait_all(); return; }
+    // the epilogue's pixel loads are issued first and land during the staging and the FFT
+    constexpr bool TWO = HasIn<F>::value && (ROWS * NX) % NT == 0 && ROWS * NX / NT <= 4;
+    constexpr int PPT = TWO ? ROWS * NX / NT : 1;
+    using InT = typename InOf<F, TWO>::type;
+    InT in[PPT];
+    if constexpr (TWO) {
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            const int t = threadIdx.x + j * NT;
+            in[j] = F::load(d, ctx, (size_t)(y0 + t / NX) * NX + t % NX);
+        }
+    }
     const C* twN = tws + M;
     const size_t plane = (size_t)d.ny * d.wp;
     // complex-to-real pre-processing: Z[k] = A + i B,
@@ -331,28 +362,33 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
     }
     __syncthreads();
     fft_smem<T, M, Cfg::NSEQ, SP, NT, true>(buf, tws);
-    } else {
-        T* rz = reinterpret_cast<T*>(smem_raw);
-        for (int t = threadIdx.x; t < Cfg::NSEQ * 2 * SP; t += NT) rz[t] = T(0);
-        __syncthreads();
-    }
-    const typename F::Ctx ctx = F::prep(d);
     constexpr int NRA = F::NR > 0 ? F::NR : 1;
     Acc<T> acc[NRA];
-#pragma unroll 4
-    for (int t = threadIdx.x; t < ROWS * NX; t += NT) {
-        const int row = t / NX, x = t % NX;
-        const size_t pix = (size_t)(y0 + row) * NX + x;
-        T v[NC];
+    if constexpr (TWO) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) v[c] = rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)];
-        F::pixel(d, ctx, pix, v, &acc[0]);
+        for (int j = 0; j < PPT; ++j) {
+            const int t = threadIdx.x + j * NT;
+            const int row = t / NX, x = t % NX;
+            T v[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) v[c] = rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)];
+            F::pixel(d, ctx, (size_t)(y0 + row) * NX + x, in[j], v, &acc[0]);
+        }
+    } else {
+        (void)in;
+#pragma unroll 4
+        for (int t = threadIdx.x; t < ROWS * NX; t += NT) {
+            const int row = t / NX, x = t % NX;
+            const size_t pix = (size_t)(y0 + row) * NX + x;
+            T v[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) v[c] = rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)];
+            pixel_one<F>(d, ctx, pix, v, &acc[0]);
+        }
     }
     if constexpr (F::NR > 0) {
-        double vals[F::NR], tot[F::NR];
-#pragma unroll
-        for (int k = 0; k < F::NR; ++k) vals[k] = acc[k].get();
-        if (reduce_last<F::NR, NT>(vals, d.part, &d.ctrl->counter, gridDim.x, tot) && threadIdx.x == 0)
+        double tot[F::NR];
+        if (reduce_acc<F::NR, NT>(acc, d.part, &d.ctrl->counter, gridDim.x, tot) && threadIdx.x == 0)
             F::finalize(d, tot);
     }
 }
@@ -365,21 +401,22 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
     using C = typename CT<T>::t;
     constexpr int CW = Cfg::CWE, SP = Cfg::SP, NT = Cfg::NT;
     const Desc<T>& d = descs[blockIdx.y];
-    if (OP::skip(d)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
+    const C* tw = d.tw + NY;
+    if constexpr (Cfg::TW_SMEM) {
+        C* tws = buf + Cfg::NSEQ * SP;
+        for (int t = threadIdx.x; t < NY; t += NT) cp_async<sizeof(C)>(&tws[t], &d.tw[NY + t]);
+        tw = tws;
+    }
+    pdl_enter();
+    if (OP::skip(d)) { cp_async_wait_all(); return; }
     const int kx0 = blockIdx.x * CW;
     const size_t plane = (size_t)d.ny * d.wp;
     constexpr int TOT = NC * NY * CW;
     for (int t = threadIdx.x; t < TOT; t += NT) {
         const int j = t % CW, ky = (t / CW) % NY, c = t / (CW * NY);
         cp_async<sizeof(C)>(&buf[(c * CW + j) * SP + pidx(ky)], &d.S[c * plane + (size_t)ky * d.wp + kx0 + j]);
-    }
-    const C* tw = d.tw + NY;
-    if constexpr (Cfg::TW_SMEM) {
-        C* tws = buf + Cfg::NSEQ * SP;
-        for (int t = threadIdx.x; t < NY; t += NT) cp_async<sizeof(C)>(&tws[t], &d.tw[NY + t]);
-        tw = tws;
     }
     cp_async_wait_all();
     __syncthreads();

@@ -5,7 +5,7 @@ namespace pff {
 
 template <typename T, class F>
 static void go_elem(int nx, int ny, const Desc<T>* d, int np, cudaStream_t st) {
-    k_elem<T, F><<<dim3(elem_blocks(nx, ny, np), np), EL_NT, 0, st>>>(d);
+    launch_pdl<T>(k_elem<T, F>, dim3(elem_blocks(nx, ny, np), np), dim3(EL_NT), 0, st, d);
     count_launch();
 }
 
@@ -63,5 +63,23 @@ void launch_gather(const Desc<T>* d, int np, int* flags, void* ctrl_out, cudaStr
     count_launch();
 }
 template void launch_gather<PFF_REAL>(const Desc<PFF_REAL>*, int, int*, void*, cudaStream_t);
+
+template <typename T>
+__global__ void k_pf_cond(const Desc<T>* __restrict__ descs, int np, cudaGraphConditionalHandle h) {
+    int any = 0;
+    for (int j = threadIdx.x; j < np; j += blockDim.x) {
+        const Ctrl* c = descs[j].ctrl;
+        any |= (!__ldcg(&c->pf_a) && __ldcg(&c->pf_full)) ? 1 : 0;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+template <typename T>
+void launch_pf_cond(const Desc<T>* d, int np, cudaGraphConditionalHandle h, cudaStream_t st) {
+    k_pf_cond<T><<<1, 64, 0, st>>>(d, np, h);
+    count_launch();
+}
+template void launch_pf_cond<PFF_REAL>(const Desc<PFF_REAL>*, int, cudaGraphConditionalHandle, cudaStream_t);
 
 }  // namespace pff

@@ -11,18 +11,30 @@ constexpr int EL_NT = 256;
 template <typename T, class F>
 __global__ void __launch_bounds__(EL_NT) k_elem(const Desc<T>* __restrict__ descs) {
     const Desc<T>& d = descs[blockIdx.y];
+    pdl_enter();
+    const typename F::Ctx ctx = F::prep(d);   // issued with the skip test
     if (F::skip(d)) return;
-    const typename F::Ctx ctx = F::prep(d);
     constexpr int NRA = F::NR > 0 ? F::NR : 1;
     Acc<T> acc[NRA];
     const size_t n = (size_t)d.nx * d.ny;
-    for (size_t i = (size_t)blockIdx.x * EL_NT + threadIdx.x; i < n; i += (size_t)gridDim.x * EL_NT)
-        F::pixel(d, ctx, i, &acc[0]);
-    if constexpr (F::NR > 0) {
-        double vals[F::NR], tot[F::NR];
+    const size_t stride = (size_t)gridDim.x * EL_NT;
+    if constexpr (HasIn<F>::value) {
+        constexpr int U = 4;   // pixels whose loads are in flight together
+        for (size_t base = (size_t)blockIdx.x * EL_NT + threadIdx.x; base < n; base += U * stride) {
+            typename F::In in[U];
 #pragma unroll
-        for (int k = 0; k < F::NR; ++k) vals[k] = acc[k].get();
-        if (reduce_last<F::NR, EL_NT>(vals, d.part, &d.ctrl->counter, gridDim.x, tot) && threadIdx.x == 0)
+            for (int j = 0; j < U; ++j)
+                if (base + j * stride < n) in[j] = F::load(d, ctx, base + j * stride);
+#pragma unroll
+            for (int j = 0; j < U; ++j)
+                if (base + j * stride < n) F::pixel(d, ctx, base + j * stride, in[j], &acc[0]);
+        }
+    } else {
+        for (size_t i = (size_t)blockIdx.x * EL_NT + threadIdx.x; i < n; i += stride) F::pixel(d, ctx, i, &acc[0]);
+    }
+    if constexpr (F::NR > 0) {
+        double tot[F::NR];
+        if (reduce_acc<F::NR, EL_NT>(acc, d.part, &d.ctrl->counter, gridDim.x, tot) && threadIdx.x == 0)
             F::finalize(d, tot);
     }
 }
@@ -221,6 +233,25 @@ struct FFlagsField {   // active flag -> p[1]
 // ---------------------------------------------------------------------------
 // launch helpers
 void count_launch();
+bool pdl_on();   // launch the operator kernels with programmatic stream serialization
+
+// Launch of a kernel that begins with pdl_enter() (row, column and elementwise
+// kernels): with the attribute it may be scheduled while its predecessor runs.
+// Only FP32 kernels use it: FP64 kernels measured slower with it.
+template <typename T, typename... P, typename... A>
+inline void launch_pdl(void (*fn)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = (sizeof(T) == 4 && pdl_on()) ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, fn, args...);
+}
 bool smem_optin(const void* fn, size_t smem);
 // optional per-kernel-class event timing (see pff_timing_enable); key = family * 16 + op
 bool timing_on();
@@ -235,7 +266,7 @@ void go_row_fwd(const Desc<T>* d, int np, int ny, cudaStream_t st, int key) {
     smem_optin((const void*)fn, Cfg::SMEM);
     const bool tm = timing_on();
     if (tm) timing_begin(key, st);
-    fn<<<dim3(ny / Cfg::ROWS, np), Cfg::NT, Cfg::SMEM, st>>>(d);
+    launch_pdl<T>(fn, dim3(ny / Cfg::ROWS, np), dim3(Cfg::NT), Cfg::SMEM, st, d);
     if (tm) timing_end(key, st);
     count_launch();
 }
@@ -246,7 +277,7 @@ void go_row_inv(const Desc<T>* d, int np, int ny, cudaStream_t st, int key) {
     smem_optin((const void*)fn, Cfg::SMEM);
     const bool tm = timing_on();
     if (tm) timing_begin(key, st);
-    fn<<<dim3(ny / Cfg::ROWS, np), Cfg::NT, Cfg::SMEM, st>>>(d);
+    launch_pdl<T>(fn, dim3(ny / Cfg::ROWS, np), dim3(Cfg::NT), Cfg::SMEM, st, d);
     if (tm) timing_end(key, st);
     count_launch();
 }
@@ -257,7 +288,7 @@ void go_col(const Desc<T>* d, int np, int wp, cudaStream_t st, int key) {
     smem_optin((const void*)fn, Cfg::SMEM);
     const bool tm = timing_on();
     if (tm) timing_begin(key, st);
-    fn<<<dim3(wp / Cfg::CWE, np), Cfg::NT, Cfg::SMEM, st>>>(d);
+    launch_pdl<T>(fn, dim3(wp / Cfg::CWE, np), dim3(Cfg::NT), Cfg::SMEM, st, d);
     if (tm) timing_end(key, st);
     count_launch();
 }

@@ -18,6 +18,9 @@ template <typename T> void launch_col(int op, int nx, int ny, int wp, const Desc
 template <typename T> void launch_elem(int op, int nx, int ny, const Desc<T>* d, int np, cudaStream_t st);
 template <typename T> void launch_step_begin(const Desc<T>* d, int np, cudaStream_t st);
 template <typename T> void launch_gather(const Desc<T>* d, int np, int* flags, void* ctrl_out, cudaStream_t st);
+// sets the graph condition h to 1 when some problem of the group evaluates J v
+// explicitly in this BCCG iteration (its pf_full is set and it has not stopped)
+template <typename T> void launch_pf_cond(const Desc<T>* d, int np, cudaGraphConditionalHandle h, cudaStream_t st);
 void launch_convert_d2f(float* dst, const double* src, size_t n, cudaStream_t st);
 void launch_convert_f2d(double* dst, const float* src, size_t n, cudaStream_t st);
 

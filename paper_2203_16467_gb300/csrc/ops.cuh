@@ -155,15 +155,29 @@ struct FCgIn {
         c.split = d.k.split;
         return c;
     }
-    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[3], Acc<T>* acc) {
+    // two-phase pixel: all loads of a thread's pixels are issued before any store
+    struct In { T p[3], r[3], q[3], th[3], e[3], phi, E; };
+    __device__ static In load(const Desc<T>& d, const Ctx& c, size_t i) {
+        In a;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            a.p[k] = d.p[k][i];
+            a.r[k] = d.r[k][i];
+            a.e[k] = d.eps[k][i];
+            if (c.upd) { a.q[k] = d.q[k][i]; a.th[k] = d.th[k][i]; }
+        }
+        a.phi = d.phi[i];
+        a.E = d.E[i];
+        return a;
+    }
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, const In& a, T (&v)[3], Acc<T>* acc) {
         T r[3], p[3];
         if (c.upd) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                T pk = d.p[k][i];
-                T rk = d.r[k][i] - c.alpha * d.q[k][i];
-                d.th[k][i] += c.alpha * pk;
-                pk = rk + c.beta * pk;
+                T rk = a.r[k] - c.alpha * a.q[k];
+                d.th[k][i] = a.th[k] + c.alpha * a.p[k];
+                T pk = rk + c.beta * a.p[k];
                 d.r[k][i] = rk;
                 d.p[k][i] = pk;
                 r[k] = rk;
@@ -171,13 +185,12 @@ struct FCgIn {
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) { r[k] = d.r[k][i]; p[k] = d.p[k][i]; }
+            for (int k = 0; k < 3; ++k) { r[k] = a.r[k]; p[k] = a.p[k]; }
         }
         wdot(acc[0], r[0], r[1], r[2], r[0], r[1], r[2]);
-        T lam, mu;
-        c.lm.at(d, i, lam, mu);
-        tangent(c.split, c.eb[0] + d.eps[0][i], c.eb[1] + d.eps[1][i], c.eb[2] + d.eps[2][i],
-                hdeg(d.phi[i]), lam, mu, p[0], p[1], p[2], v);
+        T lam = c.lm.lc * a.E, mu = c.lm.mc * a.E;
+        tangent(c.split, c.eb[0] + a.e[0], c.eb[1] + a.e[1], c.eb[2] + a.e[2], hdeg(a.phi), lam, mu,
+                p[0], p[1], p[2], v);
     }
     __device__ static void finalize(const Desc<T>& d, const double* tot) {
         Ctrl* c = d.ctrl;
@@ -210,12 +223,17 @@ struct FCgOut {
     using Ctx = NoCtx;
     __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->cg_b); }
     __device__ static Ctx prep(const Desc<T>&) { return Ctx{}; }
-    __device__ static void pixel(const Desc<T>& d, const Ctx&, size_t i, T (&v)[3], Acc<T>* acc) {
-        T p0 = d.p[0][i], p1 = d.p[1][i], p2 = d.p[2][i];
-        T r0 = d.r[0][i], r1 = d.r[1][i], r2 = d.r[2][i];
+    struct In { T p[3], r[3]; };
+    __device__ static In load(const Desc<T>& d, const Ctx&, size_t i) {
+        In a;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { a.p[k] = d.p[k][i]; a.r[k] = d.r[k][i]; }
+        return a;
+    }
+    __device__ static void pixel(const Desc<T>& d, const Ctx&, size_t i, const In& a, T (&v)[3], Acc<T>* acc) {
         d.q[0][i] = v[0]; d.q[1][i] = v[1]; d.q[2][i] = v[2];
-        wdot(acc[0], p0, p1, p2, v[0], v[1], v[2]);
-        wdot(acc[1], r0, r1, r2, v[0], v[1], v[2]);
+        wdot(acc[0], a.p[0], a.p[1], a.p[2], v[0], v[1], v[2]);
+        wdot(acc[1], a.r[0], a.r[1], a.r[2], v[0], v[1], v[2]);
         wdot(acc[2], v[0], v[1], v[2], v[0], v[1], v[2]);
     }
     __device__ static void finalize(const Desc<T>& d, const double* tot) {
@@ -409,6 +427,7 @@ struct FPfInit {
         c->pf_confirm = 0;
         c->pf_since_full = 0;
         c->pf_full_iters = 0;
+        c->pf_rsel = 0;
         c->pf_last_full = rn;
         c->pf_best = rn;
         c->pf_best_it = 0;
@@ -420,10 +439,15 @@ struct FPfInit {
     }
 };
 
+// The BCCG residual r is double-buffered: the fused iterate kernel writes the
+// recurrence residual beside the previous one, which an explicit evaluation in
+// the same iteration still needs for beta.
+template <typename T> __device__ __forceinline__ T* pf_r(const Desc<T>& d, int sel) { return sel ? d.q[1] : d.th[1]; }
+
 template <typename T>
 struct FPfA1 {   // p = -r + beta p, zero on the active set; input p
     static constexpr int NR = 0;
-    struct Ctx { T beta; int upd; };
+    struct Ctx { T beta; int upd; const T* r; };
     __device__ static bool skip(const Desc<T>& d) {
         int f = ldflag(&d.ctrl->pf_b);
         if (blockIdx.x == 0 && threadIdx.x == 0) d.ctrl->pf_a = f;
@@ -433,13 +457,20 @@ struct FPfA1 {   // p = -r + beta p, zero on the active set; input p
         Ctx c;
         c.upd = ldflag(&d.ctrl->pf_it) > 0;
         c.beta = T(ldd(&d.ctrl->pf_beta));
+        c.r = pf_r(d, ldflag(&d.ctrl->pf_rsel));
         return c;
     }
-    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[1], Acc<T>*) {
-        T p = d.th[2][i];
+    struct In { T p, r; uint8_t fl; };
+    __device__ static In load(const Desc<T>& d, const Ctx& c, size_t i) {
+        In a{d.th[2][i], T(0), 0};
+        if (c.upd) { a.r = c.r[i]; a.fl = d.flags[i]; }
+        return a;
+    }
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, const In& a, T (&v)[1], Acc<T>*) {
+        T p = a.p;
         if (c.upd) {
-            p = -d.th[1][i] + c.beta * p;
-            if (d.flags[i] & 2) p = T(0);
+            p = -a.r + c.beta * p;
+            if (a.fl & 2) p = T(0);
             d.th[2][i] = p;
         }
         v[0] = p;
@@ -457,15 +488,16 @@ struct FColLapPF {
 template <typename T>
 struct FPfA3 {   // J p; p.Jp, r.p -> alpha = -(r.p)/(p.Jp)
     static constexpr int NR = 2;
-    struct Ctx { T kappa; };
+    struct Ctx { T kappa; const T* r; };
     __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
-    __device__ static Ctx prep(const Desc<T>& d) { return Ctx{T(d.k.kappa)}; }
-    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[1], Acc<T>* acc) {
-        T p = d.th[2][i];
-        T Jp = d.r[0][i] * p - c.kappa * v[0];
+    __device__ static Ctx prep(const Desc<T>& d) { return Ctx{T(d.k.kappa), pf_r(d, ldflag(&d.ctrl->pf_rsel))}; }
+    struct In { T p, a, r; };
+    __device__ static In load(const Desc<T>& d, const Ctx& c, size_t i) { return In{d.th[2][i], d.r[0][i], c.r[i]}; }
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, const In& a, T (&v)[1], Acc<T>* acc) {
+        T Jp = a.a * a.p - c.kappa * v[0];
         d.q[0][i] = Jp;
-        acc[0].addp(p, Jp);
-        acc[1].addp(d.th[1][i], p);
+        acc[0].addp(a.p, Jp);
+        acc[1].addp(a.r, a.p);
     }
     __device__ static void finalize(const Desc<T>& d, const double* tot) {
         Ctrl* c = d.ctrl;
@@ -480,32 +512,88 @@ struct FPfA3 {   // J p; p.Jp, r.p -> alpha = -(r.p)/(p.Jp)
     }
 };
 
-// v = max(v + alpha p, v_con), bound flag (elementwise).  When the projection
-// changed no value, v_new = v + alpha p exactly and the residual follows
-// R_new = R + alpha J p; the explicit J v_new (two FFT passes) is needed only when
-// a value was clamped, every PF_REFRESH iterations, or to confirm convergence.
+// Iteration end shared by the fused iterate kernel (recurrence residual) and the
+// explicit residual kernel: beta, ||r||, active count and the stopping decision.
+template <typename T>
+__device__ __forceinline__ void pf_finish(const Desc<T>& d, Ctrl* c, double rr, double rro, double nact, bool full) {
+    double den = -c->pf_rp;   // = alpha p.Jp
+    c->pf_beta = den != 0.0 ? (rr - rro) / den : 0.0;
+    c->pf_rr = rr;
+    c->pf_it += 1;
+    c->n_active = (int)nact;
+    double rn = sqrt(rr);
+    bool conv = false;
+    if (full) {
+        c->pf_full_iters += 1;
+        c->pf_since_full = 0;
+        conv = rn <= c->pf_target;
+        // FP32: a confirming evaluation that improved little on the previous explicit
+        // residual has reached the rounding level of Jv - b
+        if (!conv && sizeof(T) == 4 && c->pf_confirm && rn >= 0.5 * c->pf_last_full) conv = true;
+        c->pf_last_full = rn;
+        if (rn < c->pf_best) { c->pf_best = rn; c->pf_best_it = c->pf_it; }
+    } else {
+        c->pf_since_full += 1;
+        if (rn <= c->pf_target) c->pf_force = 1;   // confirm with an explicit residual first
+    }
+    // FP32 safety net: no new smallest explicit residual for PF_STALL iterations
+    bool stalled = sizeof(T) == 4 && c->pf_it - c->pf_best_it >= PF_STALL;
+    if (conv || stalled || c->pf_it >= d.k.max_pf || c->pf_break) {
+        if (!conv && !stalled && !c->pf_break) c->status |= 2;
+        c->pf_b = 1;
+    } else {
+        c->pf_b = 0;
+    }
+}
+
+// Fused iterate (elementwise): v = max(v + alpha p, v_con) with the bound flag,
+// and the residual by recurrence R_new = R + alpha J p, which is exact when the
+// projection changed no value.  The active set {bound and R > 0} zeroes r.  When
+// some value was clamped (or every PF_REFRESH iterations, or to confirm
+// convergence) the finalizer leaves the iteration to the explicit J v - b
+// evaluation that follows; otherwise it commits the new residual buffer.
 constexpr int PF_REFRESH = 32;
 
 template <typename T>
 struct FPfB1 {
-    static constexpr int NR = 1;
-    struct Ctx { T alpha; };
+    static constexpr int NR = 4;
+    struct Ctx { T alpha; const T* ro; T* rn; };
     __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
-    __device__ static Ctx prep(const Desc<T>& d) { return Ctx{T(ldd(&d.ctrl->pf_alpha))}; }
-    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, Acc<T>* acc) {
-        T x = d.th[0][i] + c.alpha * d.th[2][i];
-        T vc = d.r[2][i];
-        if (x < vc) { x = vc; acc[0].add(T(1)); }
+    __device__ static Ctx prep(const Desc<T>& d) {
+        int sel = ldflag(&d.ctrl->pf_rsel);
+        return Ctx{T(ldd(&d.ctrl->pf_alpha)), pf_r(d, sel), pf_r(d, sel ^ 1)};
+    }
+    struct In { T v, p, vc, R, Jp, ro; };
+    __device__ static In load(const Desc<T>& d, const Ctx& c, size_t i) {
+        return In{d.th[0][i], d.th[2][i], d.r[2][i], d.lap[i], d.q[0][i], c.ro[i]};
+    }
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, const In& a, Acc<T>* acc) {
+        T x = a.v + c.alpha * a.p;
+        if (x < a.vc) { x = a.vc; acc[0].add(T(1)); }
         d.th[0][i] = x;
-        d.flags[i] = (uint8_t)(x == vc ? 1 : 0);
+        const bool at = (x == a.vc);
+        T rn = a.R + c.alpha * a.Jp;
+        d.lap[i] = rn;
+        const bool active = at && rn > T(0);
+        if (active) rn = T(0);
+        c.rn[i] = rn;
+        d.flags[i] = (uint8_t)((at ? 1 : 0) | (active ? 2 : 0));
+        acc[1].addp(rn, rn);
+        acc[2].addp(rn, a.ro);
+        acc[3].add(active ? T(1) : T(0));
     }
     __device__ static void finalize(const Desc<T>& d, const double* tot) {
         Ctrl* c = d.ctrl;
         const bool clamped = tot[0] > 0.0;
         if (clamped) c->pf_clamp_iters += 1;   // iterations in which the clamp changed v
-        c->pf_full = clamped || c->pf_force || c->pf_since_full + 1 >= PF_REFRESH;
+        const bool full = clamped || c->pf_force || c->pf_since_full + 1 >= PF_REFRESH;
+        c->pf_full = full;
         c->pf_confirm = c->pf_force;
         c->pf_force = 0;
+        if (!full) {
+            c->pf_rsel ^= 1;
+            pf_finish(d, c, tot[1], tot[2], tot[3], false);
+        }
     }
 };
 
@@ -529,82 +617,44 @@ struct FColLapPFFull {
 };
 
 template <typename T>
-struct FPfB3 {   // R = Jv - b (explicit or by recurrence), active set {bound and R > 0}, beta, convergence
+struct FPfB3 {   // explicit R = J v - b, active set {bound and R > 0}, beta, convergence (only when pf_full)
     static constexpr int NR = 3;
-    struct Ctx { T kappa; double kd; T alpha; int full; };
-    __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
-    __device__ static bool use_fft(const Desc<T>& d) { return ldflag(&d.ctrl->pf_full); }
+    struct Ctx { T kappa; double kd; T* r; };
+    __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a) || !ldflag(&d.ctrl->pf_full); }
     __device__ static Ctx prep(const Desc<T>& d) {
-        return Ctx{T(d.k.kappa), d.k.kappa, T(ldd(&d.ctrl->pf_alpha)), ldflag(&d.ctrl->pf_full)};
+        return Ctx{T(d.k.kappa), d.k.kappa, pf_r(d, ldflag(&d.ctrl->pf_rsel))};
     }
-    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, T (&v)[1], Acc<T>* acc) {
-        T ro = d.th[1][i];
-        T rn, x = T(0), a = T(0), b = T(0), kl = T(0);
-        if (c.full) {
-            x = d.th[0][i];
-            a = d.r[0][i];
-            b = d.r[1][i];
-            kl = c.kappa * v[0];
-            rn = a * x - kl - b;
-        } else {
-            rn = d.lap[i] + c.alpha * d.q[0][i];
-        }
+    struct In { T ro, x, a, b; uint8_t fl; };
+    __device__ static In load(const Desc<T>& d, const Ctx& c, size_t i) {
+        return In{c.r[i], d.th[0][i], d.r[0][i], d.r[1][i], d.flags[i]};
+    }
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, const In& in, T (&v)[1], Acc<T>* acc) {
+        const T ro = in.ro, x = in.x, a = in.a, b = in.b, kl = c.kappa * v[0];
+        T rn = a * x - kl - b;
         d.lap[i] = rn;
-        uint8_t fl = d.flags[i];
-        bool at = fl & 1;
+        const bool at = in.fl & 1;
         bool pos = false;
         if (at) {   // the sign only matters at the bound
             if constexpr (sizeof(T) == 8) {
                 pos = rn > T(0);
-            } else if (c.full) {
+            } else {
                 // FP32 residual; decide its sign in FP64 from the same FP32 operands when it
                 // is within rounding of zero (otherwise the FP32 sign is already exact)
                 T mag = fabs(a * x) + fabs(kl) + fabs(b);
                 if (fabs(rn) > T(4e-7) * mag) pos = rn > T(0);
                 else pos = resid_positive_fp64(a, x, c.kd, v[0], b);
-            } else {
-                pos = rn > T(0);
             }
         }
-        bool active = at && pos;
+        const bool active = at && pos;
         if (active) rn = T(0);
-        d.th[1][i] = rn;
+        c.r[i] = rn;
         d.flags[i] = (uint8_t)((at ? 1 : 0) | (active ? 2 : 0));
         acc[0].addp(rn, rn);
         acc[1].addp(rn, ro);
         acc[2].add(active ? T(1) : T(0));
     }
     __device__ static void finalize(const Desc<T>& d, const double* tot) {
-        Ctrl* c = d.ctrl;
-        double rr = tot[0];
-        double den = -c->pf_rp;   // = alpha p.Jp
-        c->pf_beta = den != 0.0 ? (rr - tot[1]) / den : 0.0;
-        c->pf_rr = rr;
-        c->pf_it += 1;
-        c->n_active = (int)tot[2];
-        double rn = sqrt(rr);
-        bool conv = false;
-        if (c->pf_full) {
-            c->pf_full_iters += 1;
-            c->pf_since_full = 0;
-            conv = rn <= c->pf_target;
-            // FP32: a confirming evaluation that improved little on the previous explicit
-            // residual has reached the rounding level of Jv - b
-            if (!conv && sizeof(T) == 4 && c->pf_confirm && rn >= 0.5 * c->pf_last_full) conv = true;
-            c->pf_last_full = rn;
-        } else {
-            c->pf_since_full += 1;
-            if (rn <= c->pf_target) c->pf_force = 1;   // confirm with an explicit residual first
-        }
-        // FP32 safety net: no new smallest explicit residual for PF_STALL iterations
-        if (c->pf_full && rn < c->pf_best) { c->pf_best = rn; c->pf_best_it = c->pf_it; }
-        bool stalled = sizeof(T) == 4 && c->pf_it - c->pf_best_it >= PF_STALL;
-        if (conv || stalled || c->pf_it >= d.k.max_pf || c->pf_break) {
-            if (!conv && !stalled && !c->pf_break) c->status |= 2;
-            c->pf_b = 1;
-        } else {
-            c->pf_b = 0;
-        }
+        pf_finish(d, d.ctrl, tot[0], tot[1], tot[2], true);
     }
 };
 

@@ -96,6 +96,7 @@ _SIGS = {
     "pff_kernel_launches": (ctypes.c_ulonglong, []),
     "pff_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "pff_set_graphs": (ctypes.c_int, [ctypes.c_int]),
+    "pff_set_pdl": (ctypes.c_int, [ctypes.c_int]),
     "pff_apply_laplacian_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
                                                    ctypes.POINTER(ctypes.c_char_p)]),
     "pff_timing_reset": (ctypes.c_int, []),
@@ -162,8 +163,13 @@ def kernel_launches():
     return int(lib.pff_kernel_launches())
 
 
+def set_pdl(on=True):
+    return _check(lib.pff_set_pdl(1 if on else 0))
+
+
 def set_graphs(on=True):
-    return _check(lib.pff_set_graphs(1 if on else 0))
+    """True/1: plain graphs; 2: graphs with conditional nodes; False/0: direct launches."""
+    return _check(lib.pff_set_graphs(int(on)))
 
 
 def timing_enable(on=True):
