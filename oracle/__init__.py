@@ -21,7 +21,9 @@ Module map:
   constitutive   Lame parameters, degradation, energy splits, stresses, tangent
   mechanics      Fourier-Galerkin residual and Newton-CG (Sec. 3.1.1)
   phasefield     driving force, Jacobian J, BCCG (Sec. 3.1.2, Algorithm 1)
-  evolution      near-equilibrium load step (Algorithm 4), energies, reports
+  evolution      near-equilibrium load step (Algorithm 4), energies, reports;
+                 alternating minimisation (Algorithm 2), time-dependent steps (Algorithm 3)
+  structures     crack / void initial conditions, random and two-phase moduli (Sec. 3.3)
 """
 from .params import Params, AT1, AT2, ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE, VOLDEV, SPECTRAL_VOLDEV, CRACK_SET, DAMAGE  # noqa: F401
-from . import fourier, constitutive, mechanics, phasefield, evolution  # noqa: F401
+from . import fourier, constitutive, mechanics, phasefield, evolution, structures  # noqa: F401

@@ -14,6 +14,11 @@ E = exp(0.3 z) / mean(exp(0.3 z)).
 import numpy as np
 
 
+def white_noise(ny, nx, seed):
+    """Seeded standard normal samples, one per grid point (the xi of Sec. 3.3 before filtering)."""
+    return np.random.Generator(np.random.PCG64(seed)).standard_normal((ny, nx))
+
+
 def gaussian_field(ny, nx, lc, seed):
     """Zero-mean, unit-variance periodic Gaussian random field with correlation length lc (pixels)."""
     rng = np.random.Generator(np.random.PCG64(seed))
