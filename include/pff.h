@@ -182,10 +182,60 @@ int pff_get_params(pff_problem* h, pff_params* p);
 /* fracture: PFF_AT1|PFF_AT2; split: PFF_ISOTROPIC|PFF_SPECTRAL|PFF_SPECTRAL_STRESSFREE;
  * irreversibility: PFF_CRACK_SET|PFF_DAMAGE (Sec. 2.1, Eq. constraint_field). */
 int pff_set_model(pff_problem* h, int fracture, int split, int irreversibility);
-/* Young's modulus field E(x) > 0, nx*ny values. */
+/* Young's modulus field E(x) >= 0 with a positive mean, nx*ny values (zeros
+ * appear in the crack of pff_init_crack with PFF_IC_MODULUS). */
 int pff_set_modulus_field(pff_problem* h, const double* E, int on_device);
 /* Phase field, nx*ny values in [0, 1] (initial condition; default 0). */
 int pff_set_phase_field(pff_problem* h, const double* phi, int on_device);
+
+/* ---- Initial conditions (Sec. 4.1.1, Eq. init_crack; Sec. 4.2.2) ----
+ * Horizontal crack centred at (xc, yc) (lengths in the unit of dx; grid point
+ * (i, j) at (i dx, j dx)): phi_init = (1 - |r|/(2 ell))^2 where |r| <= 2 ell,
+ * else 0, with ell the problem's parameter and
+ *   PFF_CRACK_EDGE:    r = (max(x - length/2, 0), y), x, y from the centre, x in
+ *                      [-Lx/2, Lx/2): the equation as printed, a notch from the
+ *                      periodic cut to a rounded tip (the periodic
+ *                      single-edge-notched specimen of Sec. 3.3);
+ *   PFF_CRACK_SEGMENT: r = (max(|x| - length/2, 0), y), two rounded tips;
+ *                      length 0 is the small void of Sec. 4.1.1.
+ * target PFF_IC_PHASE_FIELD sets phi = phi_init; PFF_IC_MODULUS sets the crack
+ * in E, E = h(phi_init) E0 = (1 - phi_init)^2 E0 (replacing the modulus field).
+ * Computed on the device in FP64 on the problem's stream; synchronises it.
+ * PFF_ERR_INVALID_ARG for an unknown target or shape, length < 0, E0 <= 0. */
+enum { PFF_CRACK_SEGMENT = 0, PFF_CRACK_EDGE = 1 };
+enum { PFF_IC_PHASE_FIELD = 0, PFF_IC_MODULUS = 1 };
+int pff_init_crack(pff_problem* h, int target, int shape, double xc, double yc, double length, double E0);
+
+/* ---- Microstructure generators (Sec. 3.3) ----
+ * E = E0 xi from nx*ny standard-normal samples xi (drawn by the caller: host or
+ * device FP64, row-major), low-pass filtered in Fourier space to the modes with
+ * 0 < |q| <= 2 pi / L_cut (decided as kx^2 (Ly L_cut)^2 + ky^2 (Lx L_cut)^2 <=
+ * (Lx Ly)^2), then
+ *   PFF_MICRO_RANDOM:    xi_r = xi std_target / STD(xi) + 1 (population
+ *                        standard deviation), values below 1 mapped to
+ *                        1 - d D / (d^10 + D^10)^(1/10), d = 1 - xi_r,
+ *                        D = 1 - xi_min (Eq. sigmoid);
+ *   PFF_MICRO_TWO_PHASE: xi_p = sgn(xi), ac_iters iterations of Eq. ACsmooth
+ *                        (explicit Allen-Cahn step, periodic 5-point Laplacian in
+ *                        pixel units), xi_p := a xi_p + 1.
+ * The result replaces the problem's modulus field.  All steps run on the
+ * device in FP64 (the filter through the library's FFT passes) on the
+ * problem's stream; temporary device scratch (about 4 nx ny doubles) is
+ * allocated and freed inside the call, which synchronises the stream.
+ * pff_default_micro_params fills the paper's values: L_cut 6 (in units of
+ * ell = 1), std_target 0.3, xi_min 0.01, a 0.875, ac_iters 21, E0 1. */
+enum { PFF_MICRO_RANDOM = 0, PFF_MICRO_TWO_PHASE = 1 };
+typedef struct pff_micro_params {
+    int kind;                  /* PFF_MICRO_RANDOM or PFF_MICRO_TWO_PHASE */
+    double L_cut;              /* cutoff wavelength (unit of dx), > 0 */
+    double std_target;         /* random: target standard deviation STD_t */
+    double xi_min;             /* random: lower bound of the sigmoid floor, < 1 */
+    double a;                  /* two-phase: xi_p := a xi_p + 1, 0 < a < 1 */
+    int ac_iters;              /* two-phase: Allen-Cahn iterations, >= 0 */
+    double E0;                 /* E = E0 xi, > 0 */
+} pff_micro_params;
+int pff_default_micro_params(pff_micro_params* mp);
+int pff_generate_modulus(pff_problem* h, const pff_micro_params* mp, const double* noise, int noise_on_device);
 /* Strain state: eps_star (3 planes, may be NULL for zero) and eps_bar[3] (host). */
 int pff_set_strain(pff_problem* h, const double* eps_star, const double eps_bar[3], int on_device);
 /* Reset the near-equilibrium Flag of Algorithm 4 (set once the trigger is met). */

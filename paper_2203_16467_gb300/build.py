@@ -51,7 +51,7 @@ def build(force=False, verbose=False, jobs=None):
         for tag, real in PRECISIONS.items():
             obj = os.path.join(BUILD, tu.replace(".cu", f"_{tag}.o"))
             jobs_list.append([cc, *ARCH, *FLAGS, f"-DPFF_REAL={real}", "-c", os.path.join(CSRC, tu), "-o", obj])
-    for host_tu in ("api.cu", "noalloc.cu"):
+    for host_tu in ("api.cu", "noalloc.cu", "micro.cu"):
         jobs_list.append([cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, host_tu),
                           "-o", os.path.join(BUILD, host_tu.replace(".cu", ".o"))])
 

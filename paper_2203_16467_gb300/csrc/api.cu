@@ -141,6 +141,11 @@ struct Twiddles {
     float2* t32 = nullptr;
     double2* t64 = nullptr;
 };
+// micro.cu
+void micro_crack(double* out, int nx, int ny, double dx, double ell, double xc, double yc, double len, int shape,
+                 int modulus, double E0, cudaStream_t st);
+int micro_generate(int nx, int ny, double dx, const pff_micro_params& mp, const double* noise_dev, double* E_dev,
+                   const double2* tw64, cudaStream_t st, std::string& err);
 static const int TWN = 4096;
 static int twiddles_for(int dev, Twiddles& out) {
     static std::mutex mu;
@@ -1077,14 +1082,15 @@ int pff_set_modulus_field(pff_problem* h, const double* E, int on_device) {
         if (e != cudaSuccess) return cuda_fail(h, e, "read modulus");
         for (size_t i = 0; i < n; ++i) { s += tmp[i]; s2 += tmp[i] * tmp[i]; }
         for (size_t i = 0; i < n; ++i)
-            if (!(tmp[i] > 0.0) || !std::isfinite(tmp[i])) return fail(h, PFF_ERR_INVALID_ARG, "E must be positive and finite");
+            if (!(tmp[i] >= 0.0) || !std::isfinite(tmp[i])) return fail(h, PFF_ERR_INVALID_ARG, "E must be non-negative and finite");
     } else {
         for (size_t i = 0; i < n; ++i) {
-            if (!(E[i] > 0.0) || !std::isfinite(E[i])) return fail(h, PFF_ERR_INVALID_ARG, "E must be positive and finite");
+            if (!(E[i] >= 0.0) || !std::isfinite(E[i])) return fail(h, PFF_ERR_INVALID_ARG, "E must be non-negative and finite");
             s += E[i];
             s2 += E[i] * E[i];
         }
     }
+    if (!(s > 0.0)) return fail(h, PFF_ERR_INVALID_ARG, "E must have a positive mean");
     int rc = put_field(h, h->field[0], E, n, on_device);
     if (rc) return rc;
     h->sumE = s;
@@ -1094,6 +1100,68 @@ int pff_set_modulus_field(pff_problem* h, const double* E, int on_device) {
     h->h_ctrl->sumE2 = s2;
     if ((rc = write_ctrl(h))) return rc;
     return upload_desc(h);
+}
+
+int pff_init_crack(pff_problem* h, int target, int shape, double xc, double yc, double length, double E0) {
+    if (!h) return PFF_ERR_INVALID_ARG;
+    if (target != PFF_IC_PHASE_FIELD && target != PFF_IC_MODULUS)
+        return fail(h, PFF_ERR_INVALID_ARG, "target must be PFF_IC_PHASE_FIELD or PFF_IC_MODULUS");
+    if (shape != PFF_CRACK_SEGMENT && shape != PFF_CRACK_EDGE)
+        return fail(h, PFF_ERR_INVALID_ARG, "shape must be PFF_CRACK_SEGMENT or PFF_CRACK_EDGE");
+    if (!(length >= 0.0) || !std::isfinite(xc) || !std::isfinite(yc) || (target == PFF_IC_MODULUS && !(E0 > 0.0)))
+        return fail(h, PFF_ERR_INVALID_ARG, "length must be >= 0, the centre finite and E0 > 0");
+    const size_t n = h->n();
+    double* buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, n * 8);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(h, PFF_ERR_OOM, "crack initial condition scratch"); }
+    micro_crack(buf, h->nx, h->ny, h->prm.dx, h->prm.ell, xc, yc, length, shape, target == PFF_IC_MODULUS, E0, h->st);
+    e = cudaGetLastError();
+    int rc = e == cudaSuccess ? PFF_OK : cuda_fail(h, e, "crack initial condition");
+    if (!rc) rc = target == PFF_IC_MODULUS ? pff_set_modulus_field(h, buf, 1) : pff_set_phase_field(h, buf, 1);
+    cudaStreamSynchronize(h->st);
+    cudaFree(buf);
+    return rc;
+}
+
+int pff_default_micro_params(pff_micro_params* mp) {
+    if (!mp) return PFF_ERR_INVALID_ARG;
+    mp->kind = PFF_MICRO_RANDOM;
+    mp->L_cut = 6.0;
+    mp->std_target = 0.3;
+    mp->xi_min = 0.01;
+    mp->a = 0.875;
+    mp->ac_iters = 21;
+    mp->E0 = 1.0;
+    return PFF_OK;
+}
+
+int pff_generate_modulus(pff_problem* h, const pff_micro_params* mp, const double* noise, int noise_on_device) {
+    if (!h || !mp || !noise) return PFF_ERR_INVALID_ARG;
+    if ((mp->kind != PFF_MICRO_RANDOM && mp->kind != PFF_MICRO_TWO_PHASE) || !(mp->L_cut > 0.0) || !(mp->E0 > 0.0) ||
+        (mp->kind == PFF_MICRO_RANDOM && (!(mp->std_target > 0.0) || !(mp->xi_min < 1.0))) ||
+        (mp->kind == PFF_MICRO_TWO_PHASE && (!(mp->a > 0.0) || !(mp->a < 1.0) || mp->ac_iters < 0)))
+        return fail(h, PFF_ERR_INVALID_ARG, "invalid microstructure parameters");
+    const size_t n = h->n();
+    double *xi = nullptr, *E = nullptr;
+    cudaError_t e = cudaMalloc(&xi, n * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&E, n * 8);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(xi);
+        return fail(h, PFF_ERR_OOM, "microstructure scratch");
+    }
+    e = cudaMemcpyAsync(xi, noise, n * 8, noise_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st);
+    int rc = e == cudaSuccess ? PFF_OK : cuda_fail(h, e, "noise upload");
+    std::string err;
+    if (!rc) {
+        rc = micro_generate(h->nx, h->ny, h->prm.dx, *mp, xi, E, h->tw.t64, h->st, err);
+        if (rc) fail(h, rc, err);
+    }
+    if (!rc) rc = pff_set_modulus_field(h, E, 1);
+    cudaStreamSynchronize(h->st);
+    cudaFree(xi);
+    cudaFree(E);
+    return rc;
 }
 
 int pff_set_phase_field(pff_problem* h, const double* phi, int on_device) {

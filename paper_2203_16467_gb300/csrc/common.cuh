@@ -83,6 +83,7 @@ struct Consts {
     double inv_n;           // 1 / (nx ny)
     double L1_scale;        // (dx/ell)^2
     double two_pi_over_Lx, two_pi_over_Ly;
+    double lp_a, lp_b, lp_c;  // low-pass band kx^2 lp_a + ky^2 lp_b <= lp_c (microstructure generator only)
     int max_newton, max_cg, max_pf;
     int fracture, split, irrev;
 };

@@ -207,8 +207,9 @@ template <typename T>
 struct ModeK {
     T cx, cy, inv_n;
     int nx, ny;
+    const Consts* kc;       // the problem constants (read only by rarely used multipliers)
     __device__ __forceinline__ explicit ModeK(const Desc<T>& d)
-        : cx(T(d.k.two_pi_over_Lx)), cy(T(d.k.two_pi_over_Ly)), inv_n(T(d.k.inv_n)), nx(d.nx), ny(d.ny) {}
+        : cx(T(d.k.two_pi_over_Lx)), cy(T(d.k.two_pi_over_Ly)), inv_n(T(d.k.inv_n)), nx(d.nx), ny(d.ny), kc(&d.k) {}
 };
 
 

@@ -300,6 +300,22 @@ struct FColLapPlain {
     }
 };
 
+// Low-pass filter of the microstructure generator (Sec. 3.3): keeps the modes
+// with 0 < |q| <= 2 pi / L_cut, decided as kx^2 (Ly L_cut)^2 + ky^2 (Lx L_cut)^2
+// <= (Lx Ly)^2 with unfused FP64 products and sum.
+struct FColLowPass {
+    template <typename T> __device__ static bool skip(const Desc<T>&) { return false; }
+    template <typename T> __device__ static void apply(const ModeK<T>& m, int kx, int ky, typename CT<T>::t (&v)[1]) {
+        const int sk = signed_k(ky, m.ny);
+        const double lhs = __dadd_rn(__dmul_rn((double)kx * (double)kx, m.kc->lp_a),
+                                     __dmul_rn((double)sk * (double)sk, m.kc->lp_b));
+        const bool keep = (kx != 0 || sk != 0) && lhs <= m.kc->lp_c;
+        const T f = keep ? m.inv_n : T(0);
+        v[0].x *= f;
+        v[0].y *= f;
+    }
+};
+
 struct FColGammaPlain {
     template <typename T> __device__ static bool skip(const Desc<T>&) { return false; }
     template <typename T> __device__ static void apply(const ModeK<T>& m, int kx, int ky, typename CT<T>::t (&v)[3]) {

@@ -28,6 +28,9 @@ NEAR_EQUILIBRIUM, ALTERNATING_MIN, TIME_DEPENDENT = 0, 1, 2
 FIELD_STRAIN, FIELD_EPS_STAR, FIELD_STRESS, FIELD_PHI, FIELD_PSI_PLUS, FIELD_DRIVING_FORCE, \
     FIELD_MODULUS, FIELD_ACTIVE, FIELD_UPDATE = range(9)
 _TENSOR_FIELDS = {FIELD_STRAIN, FIELD_EPS_STAR, FIELD_STRESS}
+CRACK_SEGMENT, CRACK_EDGE = 0, 1
+IC_PHASE_FIELD, IC_MODULUS = 0, 1
+MICRO_RANDOM, MICRO_TWO_PHASE = 0, 1
 
 
 class Params(ctypes.Structure):
@@ -62,6 +65,12 @@ class StepReport(ctypes.Structure):
         return out
 
 
+class MicroParams(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("L_cut", ctypes.c_double), ("std_target", ctypes.c_double),
+                ("xi_min", ctypes.c_double), ("a", ctypes.c_double), ("ac_iters", ctypes.c_int),
+                ("E0", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _DP = ctypes.POINTER(ctypes.c_double)
 _IP = ctypes.POINTER(ctypes.c_int)
@@ -78,6 +87,10 @@ _SIGS = {
     "pff_set_modulus_field": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "pff_set_phase_field": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "pff_set_strain": (ctypes.c_int, [_P, _P, _DP, ctypes.c_int]),
+    "pff_init_crack": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double]),
+    "pff_default_micro_params": (ctypes.c_int, [ctypes.POINTER(MicroParams)]),
+    "pff_generate_modulus": (ctypes.c_int, [_P, ctypes.POINTER(MicroParams), _P, ctypes.c_int]),
     "pff_set_flag": (ctypes.c_int, [_P, ctypes.c_int]),
     "pff_step_load": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(StepReport), _IP]),
     "pff_solve_mechanics": (ctypes.c_int, [_P, ctypes.POINTER(StepReport)]),
@@ -233,6 +246,29 @@ def set_phase_field(h, phi):
     nx, ny, _ = _nxny(h)
     ptr, dev, keep = _field_arg(phi, nx * ny)
     return _check(lib.pff_set_phase_field(h, ptr, dev), h)
+
+
+def init_crack(h, target=IC_PHASE_FIELD, shape=CRACK_SEGMENT, xc=0.0, yc=0.0, length=0.0, E0=1.0):
+    return _check(lib.pff_init_crack(h, int(target), int(shape), float(xc), float(yc), float(length), float(E0)), h)
+
+
+def default_micro_params(**kw):
+    mp = MicroParams()
+    _check(lib.pff_default_micro_params(ctypes.byref(mp)))
+    for k, v in kw.items():
+        if not hasattr(mp, k):
+            raise AttributeError(k)
+        setattr(mp, k, v)
+    return mp
+
+
+def generate_modulus(h, noise, kind=MICRO_RANDOM, **kw):
+    """E = E0 xi from the white noise field (host array or CUDA FP64 tensor) by the
+    Sec. 3.3 generator of the given kind; keyword arguments override pff_micro_params."""
+    nx, ny, _ = _nxny(h)
+    mp = default_micro_params(kind=int(kind), **kw)
+    ptr, dev, keep = _field_arg(noise, nx * ny)
+    return _check(lib.pff_generate_modulus(h, ctypes.byref(mp), ptr, dev), h)
 
 
 def set_strain(h, eps_star, eps_bar):
@@ -398,6 +434,7 @@ class Problem:
     def __getattr__(self, name):
         fn = globals().get(name)
         if callable(fn) and name in ("set_modulus_field", "set_phase_field", "set_strain", "set_flag", "step_load",
+                                     "init_crack", "generate_modulus",
                                      "solve_mechanics", "solve_phase_field", "get_fields", "get_device_ptr",
                                      "apply_projection", "apply_laplacian", "constitutive", "get_params"):
             return lambda *a, **k: fn(self.h, *a, **k)

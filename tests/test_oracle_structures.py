@@ -142,3 +142,28 @@ def test_homogenised_stiffness_of_the_crack_and_void_ICs():
     void = st.phi_init(n, n, 1.0, ell, n / 2, n / 2, 0.0)
     assert abs(_cbar_2222(crack, ell) - 0.65) < 0.03
     assert _cbar_2222(void, ell) > 0.99
+
+
+def _cbar_2222_modulus(E):
+    from oracle import constitutive as cm
+    from oracle import mechanics
+    from oracle.params import ISOTROPIC, Params
+    ny, nx = E.shape
+    eb = np.array([[0.0, 0.0], [0.0, 1e-3]])
+    zero = np.zeros((ny, nx))
+    es, _ = mechanics.solve(np.zeros((ny, nx, 2, 2)), eb, zero, E, Params(split=ISOTROPIC, mech_tol=1e-6))
+    lam, mu = cm.lame(E, 0.2)
+    sig = cm.stress(eb[None, None] + es, zero, lam, mu, ISOTROPIC).mean(axis=(0, 1))
+    return sig[1, 1] / eb[1, 1] / (10.0 / 9.0)      # (lambda + 2 mu)(E0 = 1) = 10/9 at nu = 0.2
+
+
+def test_homogenised_stiffness_of_generated_structures():
+    # Sec. 4.1.2 prints C-bar_2222 = 0.94 sigma_M/eps_M for a smooth random structure
+    # (STD_t 0.3) and 0.42-0.44 for two-phase ones (a = 0.875), L_cut = 6 ell, 100 ell
+    # domains at N = 511; single realisations, so a loose band.  The random field's
+    # stiffness barely depends on resolution (128^2 here); the two-phase one depends on
+    # the 2-pixel interface width and is checked at the paper's resolution (512^2).
+    xi = white_noise(128, 128, 0)
+    assert abs(_cbar_2222_modulus(st.modulus_field("random", xi, 1.0, 6 * 1.28)) - 0.94) < 0.03
+    xi = white_noise(512, 512, 0)
+    assert abs(_cbar_2222_modulus(st.modulus_field("two_phase", xi, 1.0, 6 * 5.12)) - 0.43) < 0.03
