@@ -124,6 +124,28 @@ __device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.lau
 __device__ __forceinline__ void pdl_enter() { pdl_wait(); pdl_release(); }
 
 // ---------------------------------------------------------------------------
+// Per-block constants: thread 0 evaluates F::skip and F::prep once (control
+// block loads and FP64-to-FP32 conversions, which run on GB300's narrow FP64
+// pipe) and shares the result through shared memory.  Returns true when the
+// whole problem is skipped.  Ctx must be trivially copyable.
+template <class F, class D, class X>
+__device__ __forceinline__ bool block_prep(const D& d, X& ctx) {
+    __shared__ __align__(16) unsigned char s_raw[sizeof(X)];
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) {
+        s_skip = F::skip(d) ? 1 : 0;
+        if (!s_skip) {
+            const X c = F::prep(d);
+            memcpy(s_raw, &c, sizeof(X));
+        }
+    }
+    __syncthreads();
+    if (s_skip) return true;
+    memcpy(&ctx, s_raw, sizeof(X));
+    return false;
+}
+
+// ---------------------------------------------------------------------------
 // flag access (bypass L1: flags are written by other kernels / blocks)
 __device__ __forceinline__ int ldflag(const int* p) { return __ldcg(p); }
 __device__ __forceinline__ double ldd(const double* p) { return __ldcg(p); }

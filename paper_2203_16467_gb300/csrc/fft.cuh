@@ -177,6 +177,10 @@ struct RowCfg {
     // already gives 128+ blocks per component plane
     static constexpr int ROWS = pow2floor(cmax(1, cmin(16, 512 / (NC * M))));   // divides every ny >= 16
     static constexpr int NT = (NC * ROWS * M >= 1024) ? 256 : 128;
+    // FP32 forward passes: ask the register allocator for 8 resident 128-thread
+    // blocks per SM (64 registers), so that enough loads are in flight, on the
+    // sizes where the tangent of the mechanics pass fits without spilling
+    static constexpr int MINB = (sizeof(T) == 4 && (NX == 128 || NX == 512 || NX == 1024)) ? 8 * 128 / NT : 1;
     static constexpr int SP = padded_len(M) + 2;            // pitch (complex): padded M values + slot for k = M
     static constexpr int NSEQ = NC * ROWS;
     // twiddles staged in shared memory: length-M FFT table + the M+1 real-FFT factors
@@ -208,6 +212,7 @@ struct ModeK {
     T cx, cy, inv_n;
     int nx, ny;
     const Consts* kc;       // the problem constants (read only by rarely used multipliers)
+    ModeK() = default;
     __device__ __forceinline__ explicit ModeK(const Desc<T>& d)
         : cx(T(d.k.two_pi_over_Lx)), cy(T(d.k.two_pi_over_Ly)), inv_n(T(d.k.inv_n)), nx(d.nx), ny(d.ny), kc(&d.k) {}
 };
@@ -223,11 +228,14 @@ __device__ __forceinline__ int ridx(int x) { return 2 * pidx(x >> 1) + (x & 1); 
 //   static bool skip(const Desc<T>&);             // whole-problem early exit
 //   static void pixel(const Desc<T>&, const Ctx&, size_t i, T (&v)[NC], Acc<T> (&acc)[NR]);
 //   static void finalize(const Desc<T>&, const double (&tot)[NR]);   // one thread
+#ifndef PFF_ROW_G
+#define PFF_ROW_G 2
+#endif
 template <class F, bool TWO> struct InOf { struct type {}; };
 template <class F> struct InOf<F, true> { using type = typename F::In; };
 
 template <typename T, int NX, int NC, class F>
-__global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_fwd(const Desc<T>* __restrict__ descs) {
+__global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB) k_row_fwd(const Desc<T>* __restrict__ descs) {
     using Cfg = RowCfg<T, NX, NC>;
     using C = typename CT<T>::t;
     constexpr int M = Cfg::M, SP = Cfg::SP, ROWS = Cfg::ROWS, NT = Cfg::NT;
@@ -239,14 +247,14 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_fwd(const Desc<T>
     for (int t = threadIdx.x; t < Cfg::TWS; t += NT)
         cp_async<sizeof(C)>(&tws[t], t < M ? &d.tw[M + t] : &d.tw[NX + (t - M)]);
     pdl_enter();
-    const typename F::Ctx ctx = F::prep(d);   // issued with the skip test
-    if (F::skip(d)) { cp_async_wait_all(); return; }
+    typename F::Ctx ctx;
+    if (block_prep<F>(d, ctx)) { cp_async_wait_all(); return; }
     const int y0 = blockIdx.x * ROWS;
     constexpr int NRA = F::NR > 0 ? F::NR : 1;
     Acc<T> acc[NRA];
     if constexpr (HasIn<F>::value && (ROWS * NX) % NT == 0) {
         constexpr int PPT = ROWS * NX / NT;
-        constexpr int G = PPT < 4 ? PPT : 4;   // pixels whose loads are in flight together
+        constexpr int G = PPT < PFF_ROW_G ? PPT : PFF_ROW_G;   // pixels whose loads are in flight together
 #pragma unroll
         for (int j0 = 0; j0 < PPT; j0 += G) {
             typename F::In in[G];
@@ -314,8 +322,8 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
     for (int t = threadIdx.x; t < Cfg::TWS; t += NT)
         cp_async<sizeof(C)>(&tws[t], t < M ? &d.tw[M + t] : &d.tw[NX + (t - M)]);
     pdl_enter();
-    const typename F::Ctx ctx = F::prep(d);   // issued with the skip test
-    if (F::skip(d)) { cp_async_wait_all(); return; }
+    typename F::Ctx ctx;
+    if (block_prep<F>(d, ctx)) { cp_async_wait_all(); return; }
     // the epilogue's pixel loads are issued first and land during the staging and the FFT
     constexpr bool TWO = HasIn<F>::value && (ROWS * NX) % NT == 0 && ROWS * NX / NT <= 4;
     constexpr int PPT = TWO ? ROWS * NX / NT : 1;
@@ -396,6 +404,13 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
 
 // Column pass: CWE adjacent columns kx of the half spectrum, all NC planes.
 // OP::apply(d, kx, ky, vals[NC]) multiplies one mode (normalisation included).
+// skip test and mode constants of a column pass, evaluated once per block
+template <typename T, class OP>
+struct ColPrep {
+    __device__ static bool skip(const Desc<T>& d) { return OP::skip(d); }
+    __device__ static ModeK<T> prep(const Desc<T>& d) { return ModeK<T>(d); }
+};
+
 template <typename T, int NY, int NC, class OP>
 __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __restrict__ descs) {
     using Cfg = ColCfg<T, NY, NC>;
@@ -411,7 +426,8 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
         tw = tws;
     }
     pdl_enter();
-    if (OP::skip(d)) { cp_async_wait_all(); return; }
+    ModeK<T> mk;
+    if (block_prep<ColPrep<T, OP>>(d, mk)) { cp_async_wait_all(); return; }
     const int kx0 = blockIdx.x * CW;
     const size_t plane = (size_t)d.ny * d.wp;
     constexpr int TOT = NC * NY * CW;
@@ -422,7 +438,6 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
     cp_async_wait_all();
     __syncthreads();
     fft_smem<T, NY, Cfg::NSEQ, SP, NT, false>(buf, tw);
-    const ModeK<T> mk(d);
     for (int t = threadIdx.x; t < CW * NY; t += NT) {
         const int ky = t % NY, j = t / NY;
         C v[NC];

@@ -12,8 +12,8 @@ template <typename T, class F>
 __global__ void __launch_bounds__(EL_NT) k_elem(const Desc<T>* __restrict__ descs) {
     const Desc<T>& d = descs[blockIdx.y];
     pdl_enter();
-    const typename F::Ctx ctx = F::prep(d);   // issued with the skip test
-    if (F::skip(d)) return;
+    typename F::Ctx ctx;
+    if (block_prep<F>(d, ctx)) return;
     constexpr int NRA = F::NR > 0 ? F::NR : 1;
     Acc<T> acc[NRA];
     const size_t n = (size_t)d.nx * d.ny;

@@ -25,6 +25,7 @@ constexpr int PF_STALL = 64;    // FP32 BCCG: iterations without a new smallest 
 template <typename T>
 struct LameC {
     T lc, mc;
+    LameC() = default;
     __device__ __forceinline__ explicit LameC(const Desc<T>& d) : lc(T(d.k.lam_c)), mc(T(d.k.mu_c)) {}
     __device__ __forceinline__ void at(const Desc<T>& d, size_t i, T& lam, T& mu) const {
         T E = d.E[i];
