@@ -52,6 +52,34 @@ def eps_m():
     return eps_M(1.0, NU, 1.0, ELL)
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+KERNEL_SOURCES = ("common.cuh", "fft.cuh", "ops.cuh", "kernels.cuh", "k_rowfwd.cu", "k_rowinv.cu", "k_col.cu",
+                  "k_elem.cu", "launch.h")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2203_16467_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """DRAM bytes (read + write) per launch of the kernel class from the committed ncu summary,
+    or None when there is none or the kernel sources changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    if not k or d.get("source_hash") != kernel_source_hash():
+        return None
+    return k["dram_bytes_per_launch"]
+
+
 def hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -359,7 +387,8 @@ def run_ours(args, rank, world, dev):
             "step_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
-                         "frac": (ach / peak) if ach else None, "peak_kind": peak_kind, "traffic": None},
+                         "frac": (ach / peak) if ach else None, "peak_kind": peak_kind,
+                         "traffic": measured_traffic(dom)},
             "kernels": kernels,
             "kernel_timing": f"CUDA events around each launch, over {ki} further load steps of the run with all "
                              f"eight simulations in one launch group on one stream (direct launches queued behind "
