@@ -457,6 +457,127 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
 }
 
 // ---------------------------------------------------------------------------
+// Column pass for ny = 512 with register-resident radix-8 stages (512 = 8 x 8 x 8).
+// Thread (column j, lane t) loads rows t + 64 m (m < 8) of every component
+// straight into registers and runs the three radix-8 stages with two
+// shared-memory exchanges:
+//   stage 1: DFT8 over m, twiddle W512^(n0 k1)           (n0 = the lane's index)
+//   stage 2: lane (k1, a): DFT8 over b of stage-1 values at n0 = a + 8 b, twiddle W64^(a c)
+//   stage 3: lane (k1, c): DFT8 over a -> modes k1 + 8 c + 64 e, e < 8
+// (k1 = t / 8, a or c = t % 8).  The mode multiplier acts on the NC components a
+// lane holds; the inverse runs the same stages with lane index t' = k1 + 8 c (the
+// lane holds modes t' + 64 e) and ends on rows t' + 64 e, stored straight from
+// registers.  Exchange layouts (per component and column, stride COL512_XS = 8
+// mod 16 complex slots): stage-1 value (k1, n0) at 72 k1 + n0 + n0/8, stage-2
+// value (k1, a, c) at 72 k1 + 9 a + c; every access of a warp touches each
+// bank pair at most twice (FP32).
+constexpr int COL512_CW = 4;       // columns per block (one 32-byte sector per row in FP32)
+constexpr int COL512_XS = 584;     // exchange slots per component and column
+
+template <typename C, bool INV>
+__device__ __forceinline__ void tw8(const C* tws, int base, C (&w)[8]) {
+    // W512^(base r) for r < 8 from the entries for r = 1, 2, 4 (conjugated for the inverse)
+    C w1 = tws[base], w2 = tws[2 * base], w4 = tws[4 * base];
+    if (INV) { w1.y = -w1.y; w2.y = -w2.y; w4.y = -w4.y; }
+    const C w3 = cmul(w1, w2);
+    w[1] = w1; w[2] = w2; w[3] = w3; w[4] = w4;
+    w[5] = cmul(w1, w4); w[6] = cmul(w2, w4); w[7] = cmul(w3, w4);
+}
+
+template <typename T, bool INV, int NC>
+__device__ __forceinline__ void fft512_reg(typename CT<T>::t (&u)[NC][8], int n0, int t, typename CT<T>::t* xb,
+                                           const typename CT<T>::t* tws) {
+    using C = typename CT<T>::t;
+    constexpr int CS = COL512_CW * COL512_XS;   // component stride
+    C w[8];
+    // stage 1
+    tw8<C, INV>(tws, n0, w);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        dft8<C, INV>(u[c]);
+#pragma unroll
+        for (int r = 1; r < 8; ++r) u[c][r] = cmul(u[c][r], w[r]);
+    }
+    __syncthreads();   // earlier readers of xb are done
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int k1 = 0; k1 < 8; ++k1) xb[c * CS + 72 * k1 + n0 + (n0 >> 3)] = u[c][k1];
+    __syncthreads();
+    // stage 2
+    const int k1 = t >> 3, a = t & 7;
+    tw8<C, INV>(tws, 8 * a, w);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+        for (int b = 0; b < 8; ++b) u[c][b] = xb[c * CS + 72 * k1 + a + 9 * b];
+        dft8<C, INV>(u[c]);
+#pragma unroll
+        for (int r = 1; r < 8; ++r) u[c][r] = cmul(u[c][r], w[r]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) xb[c * CS + 72 * k1 + 9 * a + cc] = u[c][cc];
+    __syncthreads();
+    // stage 3 (lane (k1, c) with c = a)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+        for (int aa = 0; aa < 8; ++aa) u[c][aa] = xb[c * CS + 72 * k1 + 9 * aa + a];
+        dft8<C, INV>(u[c]);
+    }
+}
+
+template <typename T, int NC>
+struct Col512Cfg {
+    static constexpr int NT = 64 * COL512_CW;
+    static constexpr size_t SMEM = (size_t)(512 + NC * COL512_CW * COL512_XS) * sizeof(typename CT<T>::t);
+};
+
+template <typename T, int NC, class OP>
+__global__ void __launch_bounds__(64 * COL512_CW) k_col512(const Desc<T>* __restrict__ descs) {
+    using C = typename CT<T>::t;
+    constexpr int N = 512;
+    const Desc<T>& d = descs[blockIdx.y];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tws = reinterpret_cast<C*>(smem_raw);   // exp(-2 pi i k / 512), k < 512
+    C* xb = tws + N;
+    for (int i = threadIdx.x; i < N; i += 64 * COL512_CW) cp_async<sizeof(C)>(&tws[i], &d.tw[N + i]);
+    pdl_enter();
+    ModeK<T> mk;
+    if (block_prep<ColPrep<T, OP>>(d, mk)) { cp_async_wait_all(); return; }
+    const int j = threadIdx.x & (COL512_CW - 1), t = threadIdx.x / COL512_CW;
+    const int kx = blockIdx.x * COL512_CW + j;
+    const size_t plane = (size_t)d.ny * d.wp;
+    C u[NC][8];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) u[c][m] = d.S[c * plane + (size_t)(t + 64 * m) * d.wp + kx];
+    cp_async_wait_all();
+    __syncthreads();
+    fft512_reg<T, false, NC>(u, t, t, xb + j * COL512_XS, tws);
+    const int k1 = t >> 3, cc = t & 7;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        C v[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v[c] = u[c][e];
+        OP::apply(mk, kx, k1 + 8 * cc + 64 * e, v);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) u[c][e] = v[c];
+    }
+    const int tp = k1 + 8 * cc;
+    fft512_reg<T, true, NC>(u, tp, t, xb + j * COL512_XS, tws);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) d.S[c * plane + (size_t)(tp + 64 * e) * d.wp + kx] = u[c][e];
+}
+
+// ---------------------------------------------------------------------------
 // mode multipliers
 // Signed wavenumber index of row ky (numpy fftfreq order); Nyquist flagged.
 __device__ __forceinline__ int signed_k(int k, int n) { return k < n / 2 ? k : k - n; }

@@ -283,12 +283,19 @@ void go_row_inv(const Desc<T>* d, int np, int ny, cudaStream_t st, int key) {
 }
 template <typename T, int NY, int NC, class OP>
 void go_col(const Desc<T>* d, int np, int wp, cudaStream_t st, int key) {
-    using Cfg = ColCfg<T, NY, NC>;
-    auto fn = k_col<T, NY, NC, OP>;
-    smem_optin((const void*)fn, Cfg::SMEM);
     const bool tm = timing_on();
     if (tm) timing_begin(key, st);
-    launch_pdl<T>(fn, dim3(wp / Cfg::CWE, np), dim3(Cfg::NT), Cfg::SMEM, st, d);
+    if constexpr (NY == 512 && sizeof(T) == 4) {   // register-resident radix-8 stages (FP64: too many registers)
+        using Cfg = Col512Cfg<T, NC>;
+        auto fn = k_col512<T, NC, OP>;
+        smem_optin((const void*)fn, Cfg::SMEM);
+        launch_pdl<T>(fn, dim3(wp / COL512_CW, np), dim3(Cfg::NT), Cfg::SMEM, st, d);
+    } else {
+        using Cfg = ColCfg<T, NY, NC>;
+        auto fn = k_col<T, NY, NC, OP>;
+        smem_optin((const void*)fn, Cfg::SMEM);
+        launch_pdl<T>(fn, dim3(wp / Cfg::CWE, np), dim3(Cfg::NT), Cfg::SMEM, st, d);
+    }
     if (tm) timing_end(key, st);
     count_launch();
 }
