@@ -70,7 +70,9 @@ __device__ __forceinline__ void dft8(C (&u)[8]) {
 //   butterfly i in [0, M/R): k = i mod p; inputs x[i + r M/R]; twiddle
 //   w^(r k) with w = exp(-+2 pi i/(p R)); outputs y[(i - k) R + k + r p].
 // Twiddles: w^k, w^2k (and w^4k for radix 8) from the table, the rest as products.
-template <typename T, int M, int R, int G, int NSEQ, int SP, int NT, bool INV>
+// TWP: the twiddle table is stored with padded indices (pidx), as when staged in
+// shared memory, so that the strided reads of a warp spread over the banks.
+template <typename T, int M, int R, int G, int NSEQ, int SP, int NT, bool INV, bool TWP = false>
 __device__ __forceinline__ void stockham_pass(typename CT<T>::t* buf, int s0, int p, const typename CT<T>::t* tw) {
     using C = typename CT<T>::t;
     constexpr int NBS = M / R;           // butterflies per sequence
@@ -95,19 +97,19 @@ __device__ __forceinline__ void stockham_pass(typename CT<T>::t* buf, int s0, in
             const int k = i & (p - 1);
             if (p > 1) {
                 const int idx = k * (M / (p * R));
-                C w1 = tw[idx];
+                C w1 = tw[TWP ? pidx(idx) : idx];
                 if (INV) w1.y = -w1.y;
                 if (R == 2) {
                     u[j][1] = cmul(u[j][1], w1);
                 } else {
-                    C w2 = tw[2 * idx];
+                    C w2 = tw[TWP ? pidx(2 * idx) : 2 * idx];
                     if (INV) w2.y = -w2.y;
                     C w3 = cmul(w1, w2);
                     u[j][1] = cmul(u[j][1], w1);
                     u[j][2] = cmul(u[j][2], w2);
                     u[j][3] = cmul(u[j][3], w3);
                     if (R == 8) {
-                        C w4 = tw[4 * idx];
+                        C w4 = tw[TWP ? pidx(4 * idx) : 4 * idx];
                         if (INV) w4.y = -w4.y;
                         u[j][4] = cmul(u[j][4], w4);
                         u[j][5] = cmul(u[j][5], cmul(w1, w4));
@@ -137,7 +139,7 @@ __device__ __forceinline__ void stockham_pass(typename CT<T>::t* buf, int s0, in
 // radix-8 passes after one radix-2 or radix-4 pass when log2 M is not a multiple
 // of 3.  Sequences are processed in rounds of G; each thread holds at most PER8
 // radix-8 butterflies of a round in registers.
-template <typename T, int M, int NSEQ, int SP, int NT, bool INV>
+template <typename T, int M, int NSEQ, int SP, int NT, bool INV, bool TWP = false>
 __device__ __forceinline__ void fft_smem(typename CT<T>::t* buf, const typename CT<T>::t* tw) {
     constexpr int LOG = ilog2(M);
     constexpr int PER8 = sizeof(T) == 4 ? 2 : 1;
@@ -145,13 +147,13 @@ __device__ __forceinline__ void fft_smem(typename CT<T>::t* buf, const typename 
     for (int s0 = 0; s0 < NSEQ; s0 += G) {
         int p = 1;
         if (LOG % 3 == 1) {
-            stockham_pass<T, M, 2, G, NSEQ, SP, NT, INV>(buf, s0, 1, tw);
+            stockham_pass<T, M, 2, G, NSEQ, SP, NT, INV, TWP>(buf, s0, 1, tw);
             p = 2;
         } else if (LOG % 3 == 2) {
-            stockham_pass<T, M, 4, G, NSEQ, SP, NT, INV>(buf, s0, 1, tw);
+            stockham_pass<T, M, 4, G, NSEQ, SP, NT, INV, TWP>(buf, s0, 1, tw);
             p = 4;
         }
-        for (; p < M; p *= 8) stockham_pass<T, M, 8, G, NSEQ, SP, NT, INV>(buf, s0, p, tw);
+        for (; p < M; p *= 8) stockham_pass<T, M, 8, G, NSEQ, SP, NT, INV, TWP>(buf, s0, p, tw);
     }
 }
 
@@ -183,8 +185,10 @@ struct RowCfg {
     static constexpr int MINB = (sizeof(T) == 4 && (NX == 128 || NX == 512 || NX == 1024)) ? 8 * 128 / NT : 1;
     static constexpr int SP = padded_len(M) + 2;            // pitch (complex): padded M values + slot for k = M
     static constexpr int NSEQ = NC * ROWS;
-    // twiddles staged in shared memory: length-M FFT table + the M+1 real-FFT factors
-    static constexpr int TWS = 2 * M + 1;
+    // twiddles staged in shared memory: length-M FFT table (padded indices) + the
+    // M+1 real-FFT factors
+    static constexpr int TWF = padded_len(M);
+    static constexpr int TWS = TWF + M + 1;
     static constexpr size_t SMEM = (size_t)(NSEQ * SP + TWS) * sizeof(typename CT<T>::t);
 };
 
@@ -199,8 +203,8 @@ struct ColCfg {
     static constexpr int NSEQ = NC * CWE;
     static constexpr int NT = (NSEQ * NY >= 8192) ? 512 : (NSEQ * NY >= 2048 ? 256 : 128);
     // twiddles in shared memory when they fit next to the data (not for FP64 at 2048)
-    static constexpr bool TW_SMEM = (size_t)(NSEQ * SP + NY) * CSZ <= 225 * 1024;
-    static constexpr size_t SMEM = (size_t)(NSEQ * SP + (TW_SMEM ? NY : 0)) * CSZ;
+    static constexpr bool TW_SMEM = (size_t)(NSEQ * SP + padded_len(NY)) * CSZ <= 225 * 1024;
+    static constexpr size_t SMEM = (size_t)(NSEQ * SP + (TW_SMEM ? padded_len(NY) : 0)) * CSZ;
 };
 
 constexpr int WP_ALIGN = 16;   // spectral row pitch multiple (largest column tile)
@@ -243,9 +247,9 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     T* rb = reinterpret_cast<T*>(smem_raw);
-    C* tws = buf + Cfg::NSEQ * SP;          // [0, M): FFT table of length M; [M, 2M]: exp(-2 pi i k / NX)
-    for (int t = threadIdx.x; t < Cfg::TWS; t += NT)
-        cp_async<sizeof(C)>(&tws[t], t < M ? &d.tw[M + t] : &d.tw[NX + (t - M)]);
+    C* tws = buf + Cfg::NSEQ * SP;          // FFT table of length M at pidx(j); then exp(-2 pi i k / NX), k <= M
+    for (int t = threadIdx.x; t < M + M + 1; t += NT)
+        cp_async<sizeof(C)>(t < M ? &tws[pidx(t)] : &tws[Cfg::TWF + (t - M)], t < M ? &d.tw[M + t] : &d.tw[NX + (t - M)]);
     pdl_enter();
     typename F::Ctx ctx;
     if (block_prep<F>(d, ctx)) { cp_async_wait_all(); return; }
@@ -291,9 +295,9 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB
     }
     cp_async_wait_all();
     __syncthreads();
-    fft_smem<T, M, Cfg::NSEQ, SP, NT, false>(buf, tws);
+    fft_smem<T, M, Cfg::NSEQ, SP, NT, false, true>(buf, tws);
     // real-to-complex post-processing: X[k] = Xe[k] + W_N^k Xo[k], k = 0..M
-    const C* twN = tws + M;
+    const C* twN = tws + Cfg::TWF;
     const size_t plane = (size_t)d.ny * d.wp;
     for (int t = threadIdx.x; t < Cfg::NSEQ * (M + 1); t += NT) {
         const int s = t / (M + 1), k = t % (M + 1);
@@ -319,8 +323,8 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
     const T* rb = reinterpret_cast<const T*>(smem_raw);
     C* tws = buf + Cfg::NSEQ * SP;
     const int y0 = blockIdx.x * ROWS;
-    for (int t = threadIdx.x; t < Cfg::TWS; t += NT)
-        cp_async<sizeof(C)>(&tws[t], t < M ? &d.tw[M + t] : &d.tw[NX + (t - M)]);
+    for (int t = threadIdx.x; t < M + M + 1; t += NT)
+        cp_async<sizeof(C)>(t < M ? &tws[pidx(t)] : &tws[Cfg::TWF + (t - M)], t < M ? &d.tw[M + t] : &d.tw[NX + (t - M)]);
     pdl_enter();
     typename F::Ctx ctx;
     if (block_prep<F>(d, ctx)) { cp_async_wait_all(); return; }
@@ -336,7 +340,7 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
             in[j] = F::load(d, ctx, (size_t)(y0 + t / NX) * NX + t % NX);
         }
     }
-    const C* twN = tws + M;
+    const C* twN = tws + Cfg::TWF;
     const size_t plane = (size_t)d.ny * d.wp;
     // complex-to-real pre-processing: Z[k] = A + i B,
     //   A = X[k] + conj(X[M-k]),  B = (X[k] - conj(X[M-k])) e^{+2 pi i k/N}
@@ -370,7 +374,7 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
         if ((Cfg::NSEQ * M) % NT == 0 || t < Cfg::NSEQ * M) buf[(t / M) * SP + pidx(t % M)] = z[u];
     }
     __syncthreads();
-    fft_smem<T, M, Cfg::NSEQ, SP, NT, true>(buf, tws);
+    fft_smem<T, M, Cfg::NSEQ, SP, NT, true, true>(buf, tws);
     constexpr int NRA = F::NR > 0 ? F::NR : 1;
     Acc<T> acc[NRA];
     if constexpr (TWO) {
@@ -422,7 +426,7 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
     const C* tw = d.tw + NY;
     if constexpr (Cfg::TW_SMEM) {
         C* tws = buf + Cfg::NSEQ * SP;
-        for (int t = threadIdx.x; t < NY; t += NT) cp_async<sizeof(C)>(&tws[t], &d.tw[NY + t]);
+        for (int t = threadIdx.x; t < NY; t += NT) cp_async<sizeof(C)>(&tws[pidx(t)], &d.tw[NY + t]);
         tw = tws;
     }
     pdl_enter();
@@ -437,7 +441,7 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
     }
     cp_async_wait_all();
     __syncthreads();
-    fft_smem<T, NY, Cfg::NSEQ, SP, NT, false>(buf, tw);
+    fft_smem<T, NY, Cfg::NSEQ, SP, NT, false, Cfg::TW_SMEM>(buf, tw);
     for (int t = threadIdx.x; t < CW * NY; t += NT) {
         const int ky = t % NY, j = t / NY;
         C v[NC];
@@ -448,7 +452,7 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
         for (int c = 0; c < NC; ++c) buf[(c * CW + j) * SP + pidx(ky)] = v[c];
     }
     __syncthreads();
-    fft_smem<T, NY, Cfg::NSEQ, SP, NT, true>(buf, tw);
+    fft_smem<T, NY, Cfg::NSEQ, SP, NT, true, Cfg::TW_SMEM>(buf, tw);
 #pragma unroll 4
     for (int t = threadIdx.x; t < TOT; t += NT) {
         const int j = t % CW, ky = (t / CW) % NY, c = t / (CW * NY);
@@ -476,8 +480,10 @@ constexpr int COL512_XS = 584;     // exchange slots per component and column
 
 template <typename C, bool INV>
 __device__ __forceinline__ void tw8(const C* tws, int base, C (&w)[8]) {
-    // W512^(base r) for r < 8 from the entries for r = 1, 2, 4 (conjugated for the inverse)
-    C w1 = tws[base], w2 = tws[2 * base], w4 = tws[4 * base];
+    // W512^(base r) for r < 8 from the entries for r = 1, 2, 4 (conjugated for the
+    // inverse); the staged table is padded like the sequences (pidx), so that the
+    // strided reads of a warp do not collide in the shared-memory banks
+    C w1 = tws[pidx(base)], w2 = tws[pidx(2 * base)], w4 = tws[pidx(4 * base)];
     if (INV) { w1.y = -w1.y; w2.y = -w2.y; w4.y = -w4.y; }
     const C w3 = cmul(w1, w2);
     w[1] = w1; w[2] = w2; w[3] = w3; w[4] = w4;
@@ -533,7 +539,7 @@ __device__ __forceinline__ void fft512_reg(typename CT<T>::t (&u)[NC][8], int n0
 template <typename T, int NC>
 struct Col512Cfg {
     static constexpr int NT = 64 * COL512_CW;
-    static constexpr size_t SMEM = (size_t)(512 + NC * COL512_CW * COL512_XS) * sizeof(typename CT<T>::t);
+    static constexpr size_t SMEM = (size_t)(padded_len(512) + NC * COL512_CW * COL512_XS) * sizeof(typename CT<T>::t);
 };
 
 template <typename T, int NC, class OP>
@@ -542,9 +548,9 @@ __global__ void __launch_bounds__(64 * COL512_CW) k_col512(const Desc<T>* __rest
     constexpr int N = 512;
     const Desc<T>& d = descs[blockIdx.y];
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* tws = reinterpret_cast<C*>(smem_raw);   // exp(-2 pi i k / 512), k < 512
-    C* xb = tws + N;
-    for (int i = threadIdx.x; i < N; i += 64 * COL512_CW) cp_async<sizeof(C)>(&tws[i], &d.tw[N + i]);
+    C* tws = reinterpret_cast<C*>(smem_raw);   // exp(-2 pi i k / 512) at pidx(k), k < 512
+    C* xb = tws + padded_len(N);
+    for (int i = threadIdx.x; i < N; i += 64 * COL512_CW) cp_async<sizeof(C)>(&tws[pidx(i)], &d.tw[N + i]);
     pdl_enter();
     ModeK<T> mk;
     if (block_prep<ColPrep<T, OP>>(d, mk)) { cp_async_wait_all(); return; }
