@@ -339,6 +339,21 @@ int pff_set_graphs(int on);
  * device.  No counterpart in the paper (an execution detail of this library). */
 int pff_set_pdl(int on);
 
+/* Solve the phase-field sub-problem of a single FP32 512 x 512 problem (a
+ * problem, or a batch group of one) in one persistent cooperative launch
+ * (default off): the BCCG iterations of Algorithm 1 run without kernel
+ * boundaries, their phases separated by grid barriers that carry the
+ * reductions.  Measured slower than the per-phase kernels on GB300 (94.6 vs
+ * 39.4 us per iteration of one simulation when the launch takes an eighth of
+ * the device, as it must for eight simulations to run side by side), because a
+ * phase then runs several row items one after another per block.  The
+ * summation order of the dot products differs from the per-phase kernels (both
+ * are deterministic).  Barrier waits are bounded (about two seconds); a
+ * timeout ends the solve with PFF_ERR_BARRIER_TIMEOUT.  When the device cannot
+ * host the launch the per-phase kernels run instead.  Synchronises the device.
+ * No counterpart in the paper. */
+int pff_set_persistent(int on);
+
 /* Kernel timing for benchmarks.  When enabled, every launch of the library is
  * bracketed by CUDA events on its own stream; pff_timing_read returns the
  * summed device time (ms) and the launch count of one kernel class since the

@@ -54,6 +54,10 @@ def build(force=False, verbose=False, jobs=None):
     for host_tu in ("api.cu", "noalloc.cu", "micro.cu"):
         jobs_list.append([cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, host_tu),
                           "-o", os.path.join(BUILD, host_tu.replace(".cu", ".o"))])
+    # persistent kernels: their blocks read what other blocks of the same launch wrote,
+    # so global loads bypass L1 (-dlcm=cg) and 8-byte staging copies use L2-only loads
+    jobs_list.append([cc, *ARCH, *FLAGS, "-DPFF_REAL=float", "-DPFF_L2_ONLY", "-Xptxas", "-dlcm=cg", "-c",
+                      os.path.join(CSRC, "k_persist.cu"), "-o", os.path.join(BUILD, "k_persist.o")])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

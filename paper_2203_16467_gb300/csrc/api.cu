@@ -141,6 +141,9 @@ struct Twiddles {
     float2* t32 = nullptr;
     double2* t64 = nullptr;
 };
+// k_persist.cu
+int persist_bccg_blocks(int share_den);
+cudaError_t launch_persist_bccg(const Desc<float>* d, int max_iters, int blocks, cudaStream_t st);
 // micro.cu
 void micro_crack(double* out, int nx, int ny, double dx, double ell, double xc, double yc, double len, int shape,
                  int modulus, double E0, cudaStream_t st);
@@ -392,6 +395,8 @@ struct Group {
 static const int CHUNK = 8;
 static bool g_graphs_enabled = true;
 static bool g_cond_nodes = false;  // BCCG explicit-residual chain in conditional graph nodes
+static bool g_persist = false;     // persistent BCCG solve for single FP32 512^2 problems (opt-in)
+static int g_persist_share = 8;    // the persistent launch takes 1/share of the resident capacity
 
 template <typename T>
 static void chunk_direct(int kind, const Group& g) {
@@ -605,12 +610,29 @@ static void lap_phi_group(Group& g, bool with_df) {
     if (with_df) launch_elem<T>(EL_DF, g.nx, g.ny, d, g.np, g.st);
 }
 
-// Phase-field sub-problem (Algorithm 1) followed by the post-step kernel.
+// Phase-field sub-problem (Algorithm 1) followed by the post-step kernel.  A
+// single FP32 512 x 512 problem runs the whole solve in one persistent
+// cooperative launch (k_persist.cu) when enabled; otherwise chunks of CHUNK
+// iterations are launched (graph replays) and polled.
 template <typename T>
 static int pf_solve_group(Group& g, int max_pf, pff_problem* eh, bool& warmed) {
     const Desc<T>* d = (const Desc<T>*)g.d_desc;
     int rc;
     launch_elem<T>(EL_PF_INIT, g.nx, g.ny, d, g.np, g.st);
+    if constexpr (sizeof(T) == 4) {
+        if (g_persist && g.np == 1 && g.nx == 512 && g.ny == 512 && !timing_on()) {
+            cudaError_t e = launch_persist_bccg((const Desc<float>*)g.d_desc, max_pf + 2,
+                                                persist_bccg_blocks(g_persist_share), g.st);
+            if (e == cudaSuccess) {
+                if ((rc = poll<T>(g, true, eh))) return rc;
+                if (g.h_ctrl[0].status & 8)
+                    return fail(eh, PFF_ERR_BARRIER_TIMEOUT, "persistent phase-field solve: a grid barrier timed out");
+                launch_elem<T>(EL_POST, g.nx, g.ny, d, g.np, g.st);
+                return 0;
+            }
+            cudaGetLastError();   // not launched (e.g. not enough resident capacity): chunked path
+        }
+    }
     for (int it = 0; it <= max_pf + CHUNK; it += CHUNK) {
         run_chunk<T>(1, g, warmed);
         if ((rc = poll<T>(g, false, eh))) return rc;
@@ -663,7 +685,7 @@ static void fill_report(const Ctrl& c, int split, pff_step_report* r) {
     r->inner_iters = 0;
     r->istar = c.istar;
     r->broken = c.broken;
-    r->status = c.status ? PFF_ERR_NOT_CONVERGED : PFF_OK;
+    r->status = (c.status & 8) ? PFF_ERR_BARRIER_TIMEOUT : c.status ? PFF_ERR_NOT_CONVERGED : PFF_OK;
 }
 
 static Group single_group(pff_problem* h) {
@@ -1276,6 +1298,20 @@ int pff_solve_phase_field(pff_problem* h, pff_step_report* out) {
         launch_step_begin<T>(d, 1, h->st);
         run_trio<T>(h, RF_PHI, CO_LAP_PLAIN, RI_LAP);
         launch_elem<T>(EL_PF_INIT, h->nx, h->ny, d, 1, h->st);
+        if constexpr (sizeof(T) == 4) {
+            if (g_persist && h->nx == 512 && h->ny == 512 && !timing_on()) {
+                cudaError_t e = launch_persist_bccg((const Desc<float>*)h->d_desc, p.pf_max_iter + 2,
+                                                    persist_bccg_blocks(1), h->st);
+                if (e == cudaSuccess) {
+                    int r2 = poll<T>(g, true, h);
+                    if (r2) return r2;
+                    if (g.h_ctrl[0].status & 8)
+                        return fail(h, PFF_ERR_BARRIER_TIMEOUT, "persistent phase-field solve: a grid barrier timed out");
+                    return 0;
+                }
+                cudaGetLastError();
+            }
+        }
         for (int it = 0; it <= p.pf_max_iter + CHUNK; it += CHUNK) {
             for (int c = 0; c < CHUNK; ++c) {
                 run_trio<T>(h, RF_PF_A, CO_LAP_PF, RI_PF_A);
@@ -1534,6 +1570,12 @@ int pff_set_graphs(int on) {
     cudaDeviceSynchronize();
     g_graphs_enabled = on != 0;
     g_cond_nodes = on == 2;
+    return PFF_OK;
+}
+
+int pff_set_persistent(int on) {
+    cudaDeviceSynchronize();
+    g_persist = on != 0;
     return PFF_OK;
 }
 

@@ -54,6 +54,9 @@ struct Ctrl {
     // residual recurrence: pf_full = this iteration evaluates Jv explicitly
     int pf_full, pf_force, pf_confirm, pf_since_full, pf_full_iters;
     int pf_rsel;            // the BCCG residual r lives in th[1] (0) or q[1] (1)
+    // grid barrier of the persistent BCCG kernel (arrivals, release generation, abort)
+    unsigned bar_count, bar_gen;
+    int bar_abort;
     double pf_last_full;
     // post-step (Algorithm 4 lines 12-14)
     double rep_eps_bar[3], sig_bar[3], C_bar, dphi, Fe, Ff;

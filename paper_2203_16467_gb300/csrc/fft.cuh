@@ -158,8 +158,17 @@ __device__ __forceinline__ void fft_smem(typename CT<T>::t* buf, const typename 
 }
 
 // cp.async: asynchronous global -> shared copies (no register staging)
+// (PFF_L2_ONLY: translation units whose kernels read data written by other blocks of
+// the same launch copy 8-byte elements with L2-only loads instead: cp.async.ca
+// would go through L1, which is not coherent between SMs within a kernel.)
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+#ifdef PFF_L2_ONLY
+    if constexpr (BYTES == 8) {
+        *reinterpret_cast<unsigned long long*>(smem) = __ldcg(reinterpret_cast<const unsigned long long*>(gmem));
+        return;
+    }
+#endif
     unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     if constexpr (BYTES == 16)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
@@ -238,24 +247,14 @@ __device__ __forceinline__ int ridx(int x) { return 2 * pidx(x >> 1) + (x & 1); 
 template <class F, bool TWO> struct InOf { struct type {}; };
 template <class F> struct InOf<F, true> { using type = typename F::In; };
 
+// Row-forward pass of one row group y0 (ROWS rows): pixel prologue into the
+// sequence buffer (accumulating F's reductions in acc) ...
 template <typename T, int NX, int NC, class F>
-__global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB) k_row_fwd(const Desc<T>* __restrict__ descs) {
+__device__ __forceinline__ void row_fwd_pixels(const Desc<T>& d, const typename F::Ctx& ctx, int y0,
+                                               typename CT<T>::t* buf, Acc<T>* acc) {
     using Cfg = RowCfg<T, NX, NC>;
-    using C = typename CT<T>::t;
-    constexpr int M = Cfg::M, SP = Cfg::SP, ROWS = Cfg::ROWS, NT = Cfg::NT;
-    const Desc<T>& d = descs[blockIdx.y];
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
-    T* rb = reinterpret_cast<T*>(smem_raw);
-    C* tws = buf + Cfg::NSEQ * SP;          // FFT table of length M at pidx(j); then exp(-2 pi i k / NX), k <= M
-    for (int t = threadIdx.x; t < M + M + 1; t += NT)
-        cp_async<sizeof(C)>(t < M ? &tws[pidx(t)] : &tws[Cfg::TWF + (t - M)], t < M ? &d.tw[M + t] : &d.tw[NX + (t - M)]);
-    pdl_enter();
-    typename F::Ctx ctx;
-    if (block_prep<F>(d, ctx)) { cp_async_wait_all(); return; }
-    const int y0 = blockIdx.x * ROWS;
-    constexpr int NRA = F::NR > 0 ? F::NR : 1;
-    Acc<T> acc[NRA];
+    constexpr int SP = Cfg::SP, ROWS = Cfg::ROWS, NT = Cfg::NT;
+    T* rb = reinterpret_cast<T*>(buf);
     if constexpr (HasIn<F>::value && (ROWS * NX) % NT == 0) {
         constexpr int PPT = ROWS * NX / NT;
         constexpr int G = PPT < PFF_ROW_G ? PPT : PFF_ROW_G;   // pixels whose loads are in flight together
@@ -272,7 +271,7 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB
                 const int t = threadIdx.x + (j0 + j) * NT;
                 const int row = t / NX, x = t % NX;
                 T v[NC];
-                F::pixel(d, ctx, (size_t)(y0 + row) * NX + x, in[j], v, &acc[0]);
+                F::pixel(d, ctx, (size_t)(y0 + row) * NX + x, in[j], v, acc);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)] = v[c];
             }
@@ -283,18 +282,20 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB
             const int row = t / NX, x = t % NX;
             const size_t pix = (size_t)(y0 + row) * NX + x;
             T v[NC];
-            pixel_one<F>(d, ctx, pix, v, &acc[0]);
+            pixel_one<F>(d, ctx, pix, v, acc);
 #pragma unroll
             for (int c = 0; c < NC; ++c) rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)] = v[c];
         }
     }
-    if constexpr (F::NR > 0) {
-        double tot[F::NR];
-        if (reduce_acc<F::NR, NT>(acc, d.part, &d.ctrl->counter, gridDim.x, tot) && threadIdx.x == 0)
-            F::finalize(d, tot);
-    }
-    cp_async_wait_all();
-    __syncthreads();
+}
+
+// ... then (after a barrier) the real FFT along x and the half-spectrum store.
+template <typename T, int NX, int NC>
+__device__ __forceinline__ void row_fwd_fft_store(const Desc<T>& d, int y0, typename CT<T>::t* buf,
+                                                  const typename CT<T>::t* tws) {
+    using Cfg = RowCfg<T, NX, NC>;
+    using C = typename CT<T>::t;
+    constexpr int M = Cfg::M, SP = Cfg::SP, ROWS = Cfg::ROWS, NT = Cfg::NT;
     fft_smem<T, M, Cfg::NSEQ, SP, NT, false, true>(buf, tws);
     // real-to-complex post-processing: X[k] = Xe[k] + W_N^k Xo[k], k = 0..M
     const C* twN = tws + Cfg::TWF;
@@ -312,23 +313,54 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB
     }
 }
 
-template <typename T, int NX, int NC, class F>
-__global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>* __restrict__ descs) {
+// staged row twiddles: FFT table of length M at pidx(j), then exp(-2 pi i k / NX), k <= M
+template <typename T, int NX, int NC>
+__device__ __forceinline__ void stage_row_twiddles(const Desc<T>& d, typename CT<T>::t* tws) {
     using Cfg = RowCfg<T, NX, NC>;
     using C = typename CT<T>::t;
-    constexpr int M = Cfg::M, SP = Cfg::SP, ROWS = Cfg::ROWS, NT = Cfg::NT;
+    constexpr int M = Cfg::M;
+    for (int t = threadIdx.x; t < M + M + 1; t += blockDim.x)
+        cp_async<sizeof(C)>(t < M ? &tws[pidx(t)] : &tws[Cfg::TWF + (t - M)], t < M ? &d.tw[M + t] : &d.tw[NX + (t - M)]);
+}
+
+template <typename T, int NX, int NC, class F>
+__global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB) k_row_fwd(const Desc<T>* __restrict__ descs) {
+    using Cfg = RowCfg<T, NX, NC>;
+    using C = typename CT<T>::t;
+    constexpr int NT = Cfg::NT;
     const Desc<T>& d = descs[blockIdx.y];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
-    const T* rb = reinterpret_cast<const T*>(smem_raw);
-    C* tws = buf + Cfg::NSEQ * SP;
-    const int y0 = blockIdx.x * ROWS;
-    for (int t = threadIdx.x; t < M + M + 1; t += NT)
-        cp_async<sizeof(C)>(t < M ? &tws[pidx(t)] : &tws[Cfg::TWF + (t - M)], t < M ? &d.tw[M + t] : &d.tw[NX + (t - M)]);
+    C* tws = buf + Cfg::NSEQ * Cfg::SP;
+    stage_row_twiddles<T, NX, NC>(d, tws);
     pdl_enter();
     typename F::Ctx ctx;
     if (block_prep<F>(d, ctx)) { cp_async_wait_all(); return; }
-    // the epilogue's pixel loads are issued first and land during the staging and the FFT
+    const int y0 = blockIdx.x * Cfg::ROWS;
+    constexpr int NRA = F::NR > 0 ? F::NR : 1;
+    Acc<T> acc[NRA];
+    row_fwd_pixels<T, NX, NC, F>(d, ctx, y0, buf, &acc[0]);
+    if constexpr (F::NR > 0) {
+        double tot[F::NR];
+        if (reduce_acc<F::NR, NT>(acc, d.part, &d.ctrl->counter, gridDim.x, tot) && threadIdx.x == 0)
+            F::finalize(d, tot);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    row_fwd_fft_store<T, NX, NC>(d, y0, buf, tws);
+}
+
+// Row-inverse pass of one row group y0: the epilogue's pixel loads are issued
+// first (they land during the staging and the FFT), the half-spectrum rows are
+// staged, combined for the complex-to-real transform, transformed back along x,
+// and the epilogue runs on the real values (accumulating F's reductions in acc).
+template <typename T, int NX, int NC, class F>
+__device__ __forceinline__ void row_inv_item(const Desc<T>& d, const typename F::Ctx& ctx, int y0,
+                                             typename CT<T>::t* buf, const typename CT<T>::t* tws, Acc<T>* acc) {
+    using Cfg = RowCfg<T, NX, NC>;
+    using C = typename CT<T>::t;
+    constexpr int M = Cfg::M, SP = Cfg::SP, ROWS = Cfg::ROWS, NT = Cfg::NT;
+    const T* rb = reinterpret_cast<const T*>(buf);
     constexpr bool TWO = HasIn<F>::value && (ROWS * NX) % NT == 0 && ROWS * NX / NT <= 4;
     constexpr int PPT = TWO ? ROWS * NX / NT : 1;
     using InT = typename InOf<F, TWO>::type;
@@ -375,8 +407,6 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
     }
     __syncthreads();
     fft_smem<T, M, Cfg::NSEQ, SP, NT, true, true>(buf, tws);
-    constexpr int NRA = F::NR > 0 ? F::NR : 1;
-    Acc<T> acc[NRA];
     if constexpr (TWO) {
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
@@ -385,7 +415,7 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
             T v[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) v[c] = rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)];
-            F::pixel(d, ctx, (size_t)(y0 + row) * NX + x, in[j], v, &acc[0]);
+            F::pixel(d, ctx, (size_t)(y0 + row) * NX + x, in[j], v, acc);
         }
     } else {
         (void)in;
@@ -396,9 +426,27 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
             T v[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) v[c] = rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)];
-            pixel_one<F>(d, ctx, pix, v, &acc[0]);
+            pixel_one<F>(d, ctx, pix, v, acc);
         }
     }
+}
+
+template <typename T, int NX, int NC, class F>
+__global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>* __restrict__ descs) {
+    using Cfg = RowCfg<T, NX, NC>;
+    using C = typename CT<T>::t;
+    constexpr int NT = Cfg::NT;
+    const Desc<T>& d = descs[blockIdx.y];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* tws = buf + Cfg::NSEQ * Cfg::SP;
+    stage_row_twiddles<T, NX, NC>(d, tws);
+    pdl_enter();
+    typename F::Ctx ctx;
+    if (block_prep<F>(d, ctx)) { cp_async_wait_all(); return; }
+    constexpr int NRA = F::NR > 0 ? F::NR : 1;
+    Acc<T> acc[NRA];
+    row_inv_item<T, NX, NC, F>(d, ctx, blockIdx.x * Cfg::ROWS, buf, tws, &acc[0]);
     if constexpr (F::NR > 0) {
         double tot[F::NR];
         if (reduce_acc<F::NR, NT>(acc, d.part, &d.ctrl->counter, gridDim.x, tot) && threadIdx.x == 0)
@@ -490,11 +538,11 @@ __device__ __forceinline__ void tw8(const C* tws, int base, C (&w)[8]) {
     w[5] = cmul(w1, w4); w[6] = cmul(w2, w4); w[7] = cmul(w3, w4);
 }
 
-template <typename T, bool INV, int NC>
+template <typename T, bool INV, int NC, int CW>
 __device__ __forceinline__ void fft512_reg(typename CT<T>::t (&u)[NC][8], int n0, int t, typename CT<T>::t* xb,
                                            const typename CT<T>::t* tws) {
     using C = typename CT<T>::t;
-    constexpr int CS = COL512_CW * COL512_XS;   // component stride
+    constexpr int CS = CW * COL512_XS;   // component stride
     C w[8];
     // stage 1
     tw8<C, INV>(tws, n0, w);
@@ -536,35 +584,32 @@ __device__ __forceinline__ void fft512_reg(typename CT<T>::t (&u)[NC][8], int n0
     }
 }
 
-template <typename T, int NC>
+template <typename T, int NC, int CW = COL512_CW>
 struct Col512Cfg {
-    static constexpr int NT = 64 * COL512_CW;
-    static constexpr size_t SMEM = (size_t)(padded_len(512) + NC * COL512_CW * COL512_XS) * sizeof(typename CT<T>::t);
+    static constexpr int NT = 64 * CW;
+    static constexpr size_t SMEM = (size_t)(padded_len(512) + NC * CW * COL512_XS) * sizeof(typename CT<T>::t);
 };
 
-template <typename T, int NC, class OP>
-__global__ void __launch_bounds__(64 * COL512_CW) k_col512(const Desc<T>* __restrict__ descs) {
+// staged column twiddles: exp(-2 pi i k / 512) at pidx(k), k < 512
+template <typename T>
+__device__ __forceinline__ void stage_col512_twiddles(const Desc<T>& d, typename CT<T>::t* tws) {
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) cp_async<sizeof(typename CT<T>::t)>(&tws[pidx(i)], &d.tw[512 + i]);
+}
+
+// Column pass of the CW columns kx0.. of the half spectrum (64 CW threads).
+template <typename T, int NC, class OP, int CW>
+__device__ __forceinline__ void col512_item(const Desc<T>& d, const ModeK<T>& mk, int kx0, typename CT<T>::t* xb,
+                                            const typename CT<T>::t* tws) {
     using C = typename CT<T>::t;
-    constexpr int N = 512;
-    const Desc<T>& d = descs[blockIdx.y];
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* tws = reinterpret_cast<C*>(smem_raw);   // exp(-2 pi i k / 512) at pidx(k), k < 512
-    C* xb = tws + padded_len(N);
-    for (int i = threadIdx.x; i < N; i += 64 * COL512_CW) cp_async<sizeof(C)>(&tws[pidx(i)], &d.tw[N + i]);
-    pdl_enter();
-    ModeK<T> mk;
-    if (block_prep<ColPrep<T, OP>>(d, mk)) { cp_async_wait_all(); return; }
-    const int j = threadIdx.x & (COL512_CW - 1), t = threadIdx.x / COL512_CW;
-    const int kx = blockIdx.x * COL512_CW + j;
+    const int j = threadIdx.x % CW, t = threadIdx.x / CW;
+    const int kx = kx0 + j;
     const size_t plane = (size_t)d.ny * d.wp;
     C u[NC][8];
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
         for (int m = 0; m < 8; ++m) u[c][m] = d.S[c * plane + (size_t)(t + 64 * m) * d.wp + kx];
-    cp_async_wait_all();
-    __syncthreads();
-    fft512_reg<T, false, NC>(u, t, t, xb + j * COL512_XS, tws);
+    fft512_reg<T, false, NC, CW>(u, t, t, xb + j * COL512_XS, tws);
     const int k1 = t >> 3, cc = t & 7;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -576,11 +621,27 @@ __global__ void __launch_bounds__(64 * COL512_CW) k_col512(const Desc<T>* __rest
         for (int c = 0; c < NC; ++c) u[c][e] = v[c];
     }
     const int tp = k1 + 8 * cc;
-    fft512_reg<T, true, NC>(u, tp, t, xb + j * COL512_XS, tws);
+    fft512_reg<T, true, NC, CW>(u, tp, t, xb + j * COL512_XS, tws);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
         for (int e = 0; e < 8; ++e) d.S[c * plane + (size_t)(tp + 64 * e) * d.wp + kx] = u[c][e];
+}
+
+template <typename T, int NC, class OP>
+__global__ void __launch_bounds__(64 * COL512_CW) k_col512(const Desc<T>* __restrict__ descs) {
+    using C = typename CT<T>::t;
+    const Desc<T>& d = descs[blockIdx.y];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tws = reinterpret_cast<C*>(smem_raw);
+    C* xb = tws + padded_len(512);
+    stage_col512_twiddles<T>(d, tws);
+    pdl_enter();
+    ModeK<T> mk;
+    if (block_prep<ColPrep<T, OP>>(d, mk)) { cp_async_wait_all(); return; }
+    cp_async_wait_all();
+    __syncthreads();
+    col512_item<T, NC, OP, COL512_CW>(d, mk, blockIdx.x * COL512_CW, xb, tws);
 }
 
 // ---------------------------------------------------------------------------

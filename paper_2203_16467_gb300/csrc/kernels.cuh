@@ -8,6 +8,28 @@ namespace pff {
 
 constexpr int EL_NT = 256;
 
+// Elementwise work of functor F over the problem's pixels, grid-stride over the
+// launch's blocks (accumulating F's reductions in acc).
+template <typename T, class F>
+__device__ __forceinline__ void elem_items(const Desc<T>& d, const typename F::Ctx& ctx, Acc<T>* acc) {
+    const size_t n = (size_t)d.nx * d.ny;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    if constexpr (HasIn<F>::value) {
+        constexpr int U = 4;   // pixels whose loads are in flight together
+        for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += U * stride) {
+            typename F::In in[U];
+#pragma unroll
+            for (int j = 0; j < U; ++j)
+                if (base + j * stride < n) in[j] = F::load(d, ctx, base + j * stride);
+#pragma unroll
+            for (int j = 0; j < U; ++j)
+                if (base + j * stride < n) F::pixel(d, ctx, base + j * stride, in[j], acc);
+        }
+    } else {
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) F::pixel(d, ctx, i, acc);
+    }
+}
+
 template <typename T, class F>
 __global__ void __launch_bounds__(EL_NT) k_elem(const Desc<T>* __restrict__ descs) {
     const Desc<T>& d = descs[blockIdx.y];
@@ -16,22 +38,7 @@ __global__ void __launch_bounds__(EL_NT) k_elem(const Desc<T>* __restrict__ desc
     if (block_prep<F>(d, ctx)) return;
     constexpr int NRA = F::NR > 0 ? F::NR : 1;
     Acc<T> acc[NRA];
-    const size_t n = (size_t)d.nx * d.ny;
-    const size_t stride = (size_t)gridDim.x * EL_NT;
-    if constexpr (HasIn<F>::value) {
-        constexpr int U = 4;   // pixels whose loads are in flight together
-        for (size_t base = (size_t)blockIdx.x * EL_NT + threadIdx.x; base < n; base += U * stride) {
-            typename F::In in[U];
-#pragma unroll
-            for (int j = 0; j < U; ++j)
-                if (base + j * stride < n) in[j] = F::load(d, ctx, base + j * stride);
-#pragma unroll
-            for (int j = 0; j < U; ++j)
-                if (base + j * stride < n) F::pixel(d, ctx, base + j * stride, in[j], &acc[0]);
-        }
-    } else {
-        for (size_t i = (size_t)blockIdx.x * EL_NT + threadIdx.x; i < n; i += stride) F::pixel(d, ctx, i, &acc[0]);
-    }
+    elem_items<T, F>(d, ctx, &acc[0]);
     if constexpr (F::NR > 0) {
         double tot[F::NR];
         if (reduce_acc<F::NR, EL_NT>(acc, d.part, &d.ctrl->counter, gridDim.x, tot) && threadIdx.x == 0)

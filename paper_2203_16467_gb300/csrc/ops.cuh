@@ -445,6 +445,8 @@ struct FPfInit {
         c->pf_since_full = 0;
         c->pf_full_iters = 0;
         c->pf_rsel = 0;
+        c->bar_count = 0;
+        c->bar_abort = 0;
         c->pf_last_full = rn;
         c->pf_best = rn;
         c->pf_best_it = 0;

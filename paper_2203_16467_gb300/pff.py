@@ -110,6 +110,7 @@ _SIGS = {
     "pff_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "pff_set_graphs": (ctypes.c_int, [ctypes.c_int]),
     "pff_set_pdl": (ctypes.c_int, [ctypes.c_int]),
+    "pff_set_persistent": (ctypes.c_int, [ctypes.c_int]),
     "pff_apply_laplacian_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
                                                    ctypes.POINTER(ctypes.c_char_p)]),
     "pff_timing_reset": (ctypes.c_int, []),
@@ -174,6 +175,10 @@ def problem_bytes(nx, ny, precision):
 
 def kernel_launches():
     return int(lib.pff_kernel_launches())
+
+
+def set_persistent(on=True):
+    return _check(lib.pff_set_persistent(1 if on else 0))
 
 
 def set_pdl(on=True):
