@@ -66,18 +66,20 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel):
-    """DRAM bytes (read + write) per launch of the kernel class from the committed ncu summary,
-    or None when there is none or the kernel sources changed since it was taken."""
+def measured_traffic(kernel, alg_bytes_per_launch):
+    """DRAM bytes (read + write) per launch of the kernel class from the committed ncu capture
+    (one launch with every simulation active), scaled to the average launch of this run by the
+    algorithmic bytes it moves; None when there is no capture or the kernel sources changed
+    since it was taken."""
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)
     except Exception:
         return None
     k = d.get("kernels", {}).get(kernel)
-    if not k or d.get("source_hash") != kernel_source_hash():
+    if not k or d.get("source_hash") != kernel_source_hash() or not alg_bytes_per_launch:
         return None
-    return k["dram_bytes_per_launch"]
+    return k["dram_bytes_per_launch"] * alg_bytes_per_launch / k["algorithmic_bytes_per_launch"]
 
 
 def hbm_peak():
@@ -388,7 +390,8 @@ def run_ours(args, rank, world, dev):
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                          "frac": (ach / peak) if ach else None, "peak_kind": peak_kind,
-                         "traffic": measured_traffic(dom)},
+                         "traffic": measured_traffic(dom, kernels.get(dom, {}).get("alg_bytes_per_launch")),
+                         "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled to this run's average launch)"},
             "kernels": kernels,
             "kernel_timing": f"CUDA events around each launch, over {ki} further load steps of the run with all "
                              f"eight simulations in one launch group on one stream (direct launches queued behind "
