@@ -11,7 +11,7 @@ from tests.helpers import from3, rel_l2, tensor_rel_l2, to3
 
 pytestmark = pytest.mark.gpu
 
-SIZES = [(16, 16), (64, 32), (32, 128), (256, 256), (2048, 2048)]
+SIZES = [(16, 16), (64, 32), (32, 128), (256, 256), (512, 512), (64, 512), (512, 64), (2048, 2048)]
 
 
 @pytest.fixture(scope="module")
