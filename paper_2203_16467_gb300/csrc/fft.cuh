@@ -2,11 +2,15 @@
 // 2-D spectral operator F^-1 M F (Sec. 3.1: the DFT pair; the normalisation
 // 1/(nx ny) is folded into the mode multiplier M):
 //   k_row_fwd : per-pixel prologue -> real FFT along x  -> half spectrum S
-//   k_col     : FFT along y -> mode multiplier (Gamma or -|2 pi q|^2) -> inverse FFT along y
+//   k_col     : FFT along y -> mode multiplier (Gamma, -|2 pi q|^2 or the band
+//               limit) -> inverse FFT along y (k_col512: register radix-8 stages
+//               for 512-point FP32 columns)
 //   k_row_inv : half spectrum -> real inverse FFT along x -> per-pixel epilogue (+ reductions)
-// FFTs are radix-4 Stockham passes (one radix-2 pass first when log2 of the
-// length is odd), register staged and in place in shared memory, with
-// twiddles from FP64-accurate tables.
+// The kernels' bodies are per-item device functions (a row group, a column
+// group) that the persistent solve shares.  FFTs are radix-8 Stockham passes
+// (one radix-2 or radix-4 pass first when log2 of the length is not a multiple
+// of 3), register staged and in place in shared memory with padded indices,
+// with twiddles from FP64-accurate tables.
 #pragma once
 #include "common.cuh"
 
