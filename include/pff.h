@@ -294,6 +294,19 @@ int pff_batch_step(pff_batch* b, int n_steps, pff_step_report* reports, int* ste
  * shares every kernel launch and advances in lock step; different groups run
  * on their own streams and host threads and overlap on the device. */
 int pff_batch_set_group_size(pff_batch* b, int max_problems_per_group);
+/* Picks the launch grouping of a batch by measurement: for each of the
+ * n_candidates group sizes (as for pff_batch_set_group_size) it runs one
+ * untimed load step (regrouping recaptures the graphs) and steps_each timed load
+ * steps of every admitted simulation, scores the candidate by pixels x (mechanics
+ * CG + Newton + BCCG iterations) per second of wall time, and keeps the fastest
+ * (*chosen, may be NULL).  The n_candidates x (steps_each + 1) steps are
+ * ordinary load steps of the simulations (the grouping does not change any
+ * simulation's arithmetic); reports: max_slots x n_candidates x (steps_each + 1)
+ * entries, slot-major, filled up to steps_done[slot] (both may be NULL).
+ * Returns PFF_ERR_NOT_CONVERGED like pff_batch_step.  No counterpart in the
+ * paper (a tuning aid of this library). */
+int pff_batch_autotune(pff_batch* b, const int* group_sizes, int n_candidates, int steps_each, int* chosen,
+                       pff_step_report* reports, int* steps_done);
 
 /* Collocation Laplacian without any allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- for

@@ -8,6 +8,7 @@
 // flags once per chunk of iterations.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -1476,6 +1477,51 @@ int pff_batch_set_group_size(pff_batch* b, int max_problems_per_group) {
     b->groups.clear();
     b->group_cap = max_problems_per_group;
     return PFF_OK;
+}
+
+int pff_batch_autotune(pff_batch* b, const int* group_sizes, int n_candidates, int steps_each, int* chosen,
+                       pff_step_report* reports, int* steps_done) {
+    if (!b || !group_sizes || n_candidates < 1 || steps_each < 1) return PFF_ERR_INVALID_ARG;
+    for (int c = 0; c < n_candidates; ++c)
+        if (group_sizes[c] < 0) return PFF_ERR_INVALID_ARG;
+    const int per = steps_each + 1;              // one untimed step after regrouping (graph capture)
+    const int total = n_candidates * per;
+    std::vector<int> done(b->max_slots, 0);   // steps run per slot (reports stay contiguous)
+    if (steps_done)
+        for (int i = 0; i < b->max_slots; ++i) steps_done[i] = 0;
+    int status = PFF_OK, best = group_sizes[0];
+    double best_score = -1.0;
+    for (int c = 0; c < n_candidates; ++c) {
+        int rc = pff_batch_set_group_size(b, group_sizes[c]);
+        if (rc) return rc;
+        double elapsed = 0.0, work = 0.0;
+        for (int s = 0; s < per; ++s) {
+            std::vector<pff_step_report> one(b->max_slots);
+            std::vector<int> d1(b->max_slots, 0);
+            const auto t0 = std::chrono::steady_clock::now();
+            rc = pff_batch_step(b, 1, one.data(), d1.data());
+            const auto t1 = std::chrono::steady_clock::now();
+            if (rc && rc != PFF_ERR_NOT_CONVERGED) return rc;
+            if (rc) status = rc;
+            for (int i = 0; i < b->max_slots; ++i) {
+                if (!d1[i]) continue;
+                const pff_step_report& r = one[i];
+                if (reports) reports[(size_t)i * total + done[i]] = r;
+                ++done[i];
+                if (s > 0 && b->slot[i])
+                    work += (double)(r.mech_cg_iters + r.newton_iters + r.bccg_iters) * b->slot[i]->nx * b->slot[i]->ny;
+            }
+            if (s > 0) elapsed += std::chrono::duration<double>(t1 - t0).count();
+        }
+        const double score = elapsed > 0.0 ? work / elapsed : 0.0;
+        if (score > best_score) { best_score = score; best = group_sizes[c]; }
+    }
+    if (steps_done)
+        for (int i = 0; i < b->max_slots; ++i) steps_done[i] = done[i];
+    int rc = pff_batch_set_group_size(b, best);
+    if (rc) return rc;
+    if (chosen) *chosen = best;
+    return status;
 }
 
 int pff_batch_admit(pff_batch* b, pff_problem* h, int* slot) {

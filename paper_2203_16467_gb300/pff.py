@@ -106,6 +106,7 @@ _SIGS = {
     "pff_batch_release": (ctypes.c_int, [_P, ctypes.c_int]),
     "pff_batch_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(StepReport), _IP]),
     "pff_batch_set_group_size": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pff_batch_autotune": (ctypes.c_int, [_P, _IP, ctypes.c_int, ctypes.c_int, _IP, ctypes.POINTER(StepReport), _IP]),
     "pff_kernel_launches": (ctypes.c_ulonglong, []),
     "pff_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "pff_set_graphs": (ctypes.c_int, [ctypes.c_int]),
@@ -387,6 +388,19 @@ def batch_step(b, max_slots, n_steps=1):
     done = (ctypes.c_int * max_slots)()
     _check(lib.pff_batch_step(b, n_steps, reps, done), allow=(ERR_NOT_CONVERGED,))
     return [[reps[i * n_steps + s].to_dict() for s in range(done[i])] for i in range(max_slots)]
+
+
+def batch_autotune(b, max_slots, group_sizes=(1, 2, 4, 8), steps_each=2):
+    """Measure each launch grouping on real load steps and keep the fastest; returns
+    (chosen group size, per-slot lists of the step reports of the steps run)."""
+    n = len(group_sizes)
+    total = n * (steps_each + 1)
+    gs = (ctypes.c_int * n)(*[int(g) for g in group_sizes])
+    reps = (StepReport * (max_slots * total))()
+    done = (ctypes.c_int * max_slots)()
+    chosen = ctypes.c_int()
+    _check(lib.pff_batch_autotune(b, gs, n, steps_each, ctypes.byref(chosen), reps, done), allow=(ERR_NOT_CONVERGED,))
+    return chosen.value, [[reps[i * total + s].to_dict() for s in range(done[i])] for i in range(max_slots)]
 
 
 # ---------------------------------------------------------------------------- convenience wrappers
