@@ -427,6 +427,12 @@ def baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed):
                                        "3 load steps each after 1 warm-up step"}
     out["vs_plain_fp64_gpu"] = {"pixel_cg_iters_per_s": ((mech + bccg) * N * N / elapsed) / fp64_val,
                                 "load_steps_per_s": ours_steps / (f_steps / f_time)}
+    # the opt-in Fourier-Helmholtz preconditioned BCCG against Algorithm 1, both from the
+    # same start of the same eight variants, batched the way the timed region is
+    try:
+        out["preconditioned_bccg"] = precond_compare(pff, torch, sp)
+    except Exception as e:
+        out["preconditioned_bccg"] = {"error": str(e)[:200]}
     # end to end through the public API with host buffers
     ke = max(1, min(args.steps, 5))
     phi_h = np.empty((N, N))
@@ -463,6 +469,34 @@ def baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed):
         out["cpu_baseline"] = {"value": None, "unit": "pixel-CG-iters/s", "cores": 1, "kind": "oracle",
                                "sample": f"failed: {e}"}
     return out
+
+
+def precond_compare(pff, torch, sp, warm=2, steps=6):
+    res = {}
+    for pre in (0, 1):
+        probs, _ = make_problems(pff, sp, 0, pff.MIXED, VARIANTS)
+        for p in probs:
+            p.set_params(pf_precondition=pre)
+        b = pff.create_batch(len(probs), sum(pff.problem_bytes(N, N, pff.MIXED) for _ in probs), sp)
+        pff.batch_set_group_size(b, GROUP_SIZE)
+        for p in probs:
+            assert pff.batch_admit(b, p.h) is not None
+        pff.batch_step(b, len(probs), warm)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = pff.batch_step(b, len(probs), steps)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        rr = [r for o in out for r in o]
+        res[pre] = {"load_steps_per_s": len(rr) / dt, "bccg_iters": sum(r["bccg_iters"] for r in rr),
+                    "mech_cg_iters": sum(r["mech_cg_iters"] for r in rr)}
+        pff.destroy_batch(b)
+        for p in probs:
+            p.close()
+    return {"algorithm1": res[0], "preconditioned": res[1],
+            "load_steps_speedup": res[1]["load_steps_per_s"] / res[0]["load_steps_per_s"],
+            "sample": f"the eight variants from the benchmark start, {warm} warm-up and {steps} timed load steps "
+                      f"each, host wall clock around synchronised batch steps"}
 
 
 def serving_run(pff, stream, n_requests=12, rate=40.0, max_steps=20):

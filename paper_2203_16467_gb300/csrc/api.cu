@@ -204,6 +204,7 @@ struct GraphCache {
     const void* desc = nullptr;
     int np = 0;
     int cond = -1;                     // conditional-node setting the graphs were captured with
+    int precond = -1;                  // preconditioner setting the graphs were captured with
     void reset() {
         for (int k = 0; k < 2; ++k) {
             if (exec[k]) cudaGraphExecDestroy(exec[k]);
@@ -291,6 +292,7 @@ static Consts make_consts(const pff_problem* h) {
     k.max_newton = p.mech_max_newton;
     k.max_cg = p.mech_max_cg;
     k.max_pf = p.pf_max_iter;
+    k.pf_precond = p.pf_precondition != 0;
     k.fracture = h->fracture;
     k.split = h->split;
     k.irrev = h->irrev;
@@ -391,6 +393,7 @@ struct Group {
     int* h_flags;          // pinned np
     Ctrl* h_ctrl;          // pinned np
     GraphCache* graphs;    // may be null (no graphs)
+    int precond = 0;       // BCCG with the Fourier Helmholtz preconditioner (same for all problems)
 };
 
 static const int CHUNK = 8;
@@ -410,6 +413,11 @@ static void chunk_direct(int kind, const Group& g) {
             launch_col<T>(CO_GAMMA_CG, nx, ny, wp, d, np, st);
             launch_row_inv<T>(RI_CG, nx, ny, d, np, st);
         } else {
+            if (g.precond) {   // z = M^-1 r on the free set, beta
+                launch_row_fwd<T>(RF_PF_Z, nx, ny, d, np, st);
+                launch_col<T>(CO_PRECOND, nx, ny, wp, d, np, st);
+                launch_row_inv<T>(RI_PF_Z, nx, ny, d, np, st);
+            }
             launch_row_fwd<T>(RF_PF_A, nx, ny, d, np, st);
             launch_col<T>(CO_LAP_PF, nx, ny, wp, d, np, st);
             launch_row_inv<T>(RI_PF_A, nx, ny, d, np, st);
@@ -455,6 +463,12 @@ static cudaError_t capture_pf_chunk(const Group& g, cudaGraph_t* out, int* kerne
     }
     int nk = 0;
     for (int c = 0; c < CHUNK && e == cudaSuccess; ++c) {
+        if (g.precond) {
+            launch_row_fwd<T>(RF_PF_Z, nx, ny, d, np, st);
+            launch_col<T>(CO_PRECOND, nx, ny, wp, d, np, st);
+            launch_row_inv<T>(RI_PF_Z, nx, ny, d, np, st);
+            nk += 3;
+        }
         launch_row_fwd<T>(RF_PF_A, nx, ny, d, np, st);
         launch_col<T>(CO_LAP_PF, nx, ny, wp, d, np, st);
         launch_row_inv<T>(RI_PF_A, nx, ny, d, np, st);
@@ -513,11 +527,12 @@ static void run_chunk(int kind, Group& g, bool& warmed) {
         warmed = true;   // attributes (shared-memory opt-in) are set by the first direct chunk
         return;
     }
-    if (gc->desc != g.d_desc || gc->np != g.np || gc->cond != (int)g_cond_nodes) {
+    if (gc->desc != g.d_desc || gc->np != g.np || gc->cond != (int)g_cond_nodes || gc->precond != g.precond) {
         gc->reset();
         gc->desc = g.d_desc;
         gc->np = g.np;
         gc->cond = (int)g_cond_nodes;
+        gc->precond = g.precond;
     }
     if (gc->failed[kind]) {
         chunk_direct<T>(kind, g);
@@ -621,7 +636,7 @@ static int pf_solve_group(Group& g, int max_pf, pff_problem* eh, bool& warmed) {
     int rc;
     launch_elem<T>(EL_PF_INIT, g.nx, g.ny, d, g.np, g.st);
     if constexpr (sizeof(T) == 4) {
-        if (g_persist && g.np == 1 && g.nx == 512 && g.ny == 512 && !timing_on()) {
+        if (g_persist && !g.precond && g.np == 1 && g.nx == 512 && g.ny == 512 && !timing_on()) {
             cudaError_t e = launch_persist_bccg((const Desc<float>*)g.d_desc, max_pf + 2,
                                                 persist_bccg_blocks(g_persist_share), g.st);
             if (e == cudaSuccess) {
@@ -699,6 +714,7 @@ static Group single_group(pff_problem* h) {
     g.h_flags = h->h_flags;
     g.h_ctrl = h->h_ctrl;
     g.graphs = &h->graphs;
+    g.precond = h->prm.pf_precondition != 0;
     return g;
 }
 
@@ -852,7 +868,7 @@ static int td_step(pff_problem* h, pff_step_report* out) {
 
 // ---------------------------------------------------------------------------- batching
 struct BatchGroup {
-    int nx = 0, ny = 0, prec = 0;
+    int nx = 0, ny = 0, prec = 0, precond = 0;
     std::vector<int> slots;
     int cap = 0;
     void* d_desc = nullptr;
@@ -891,13 +907,13 @@ static void free_group(BatchGroup& g) {
 
 // (Re)build the groups of live problems: equal (nx, ny, precision) share launches.
 static int build_groups(pff_batch* b) {
-    std::map<std::tuple<int, int, int>, std::vector<int>> by;
+    std::map<std::tuple<int, int, int, int>, std::vector<int>> by;
     for (int i = 0; i < b->max_slots; ++i) {
         pff_problem* h = b->slot[i];
-        if (h && !h->broken) by[std::make_tuple(h->nx, h->ny, h->prec)].push_back(i);
+        if (h && !h->broken) by[std::make_tuple(h->nx, h->ny, h->prec, h->prm.pf_precondition != 0)].push_back(i);
     }
     // split each shape into launch groups of at most group_cap problems
-    std::vector<std::pair<std::tuple<int, int, int>, std::vector<int>>> parts;
+    std::vector<std::pair<std::tuple<int, int, int, int>, std::vector<int>>> parts;
     for (auto& kv : by) {
         const int cap = b->group_cap > 0 ? b->group_cap : (int)kv.second.size();
         for (size_t i0 = 0; i0 < kv.second.size(); i0 += cap)
@@ -910,10 +926,12 @@ static int build_groups(pff_batch* b) {
         g.nx = std::get<0>(kv.first);
         g.ny = std::get<1>(kv.first);
         g.prec = std::get<2>(kv.first);
+        g.precond = std::get<3>(kv.first);
         g.slots = kv.second;
         // reuse buffers of an old group of the same shape when large enough
         for (auto& old : b->groups)
-            if (old.d_desc && old.nx == g.nx && old.ny == g.ny && old.prec == g.prec && old.cap >= (int)g.slots.size()) {
+            if (old.d_desc && old.nx == g.nx && old.ny == g.ny && old.prec == g.prec && old.precond == g.precond &&
+                old.cap >= (int)g.slots.size()) {
                 g.cap = old.cap; g.d_desc = old.d_desc; g.d_flags = old.d_flags; g.d_ctrl = old.d_ctrl;
                 g.h_flags = old.h_flags; g.h_ctrl = old.h_ctrl; g.graphs = old.graphs; g.stream = old.stream;
                 old.d_desc = nullptr; old.d_flags = nullptr; old.d_ctrl = nullptr; old.h_flags = nullptr; old.h_ctrl = nullptr;
@@ -990,6 +1008,7 @@ int pff_default_params(pff_params* p) {
     p->dt_min = std::ldexp(1.0, -16);
     p->dt_max = std::ldexp(1.0, 16);
     p->dphi_max = 1.5;
+    p->pf_precondition = 0;
     return PFF_OK;
 }
 
@@ -1300,7 +1319,7 @@ int pff_solve_phase_field(pff_problem* h, pff_step_report* out) {
         run_trio<T>(h, RF_PHI, CO_LAP_PLAIN, RI_LAP);
         launch_elem<T>(EL_PF_INIT, h->nx, h->ny, d, 1, h->st);
         if constexpr (sizeof(T) == 4) {
-            if (g_persist && h->nx == 512 && h->ny == 512 && !timing_on()) {
+            if (g_persist && !h->prm.pf_precondition && h->nx == 512 && h->ny == 512 && !timing_on()) {
                 cudaError_t e = launch_persist_bccg((const Desc<float>*)h->d_desc, p.pf_max_iter + 2,
                                                     persist_bccg_blocks(1), h->st);
                 if (e == cudaSuccess) {
@@ -1315,6 +1334,7 @@ int pff_solve_phase_field(pff_problem* h, pff_step_report* out) {
         }
         for (int it = 0; it <= p.pf_max_iter + CHUNK; it += CHUNK) {
             for (int c = 0; c < CHUNK; ++c) {
+                if (p.pf_precondition) run_trio<T>(h, RF_PF_Z, CO_PRECOND, RI_PF_Z);
                 run_trio<T>(h, RF_PF_A, CO_LAP_PF, RI_PF_A);
                 launch_elem<T>(EL_PF_B, h->nx, h->ny, d, 1, h->st);
                 run_trio<T>(h, RF_PF_B, CO_LAP_PF_FULL, RI_PF_B);
@@ -1576,7 +1596,7 @@ int pff_batch_step(pff_batch* b, int n_steps, pff_step_report* reports, int* ste
             g.nx = bg.nx; g.ny = bg.ny; g.wp = wp_of(bg.nx); g.prec = bg.prec; g.np = (int)bg.slots.size();
             g.st = bg.stream ? bg.stream : b->st;
             g.d_desc = bg.d_desc; g.d_flags = bg.d_flags; g.d_ctrl = bg.d_ctrl;
-            g.h_flags = bg.h_flags; g.h_ctrl = bg.h_ctrl; g.graphs = bg.graphs;
+            g.h_flags = bg.h_flags; g.h_ctrl = bg.h_ctrl; g.graphs = bg.graphs; g.precond = bg.precond;
             rcs[gi] = run_group_step(g, p, energies, h0);
         };
         if (ng == 1) {

@@ -54,6 +54,8 @@ struct Ctrl {
     // residual recurrence: pf_full = this iteration evaluates Jv explicitly
     int pf_full, pf_force, pf_confirm, pf_since_full, pf_full_iters;
     int pf_rsel;            // the BCCG residual r lives in th[1] (0) or q[1] (1)
+    double pf_abar;         // mean of the BCCG diagonal a (preconditioner)
+    double pf_rz;           // r.z of the previous preconditioned iteration
     // grid barrier of the persistent BCCG kernel (arrivals, release generation, abort)
     unsigned bar_count, bar_gen;
     int bar_abort;
@@ -88,6 +90,7 @@ struct Consts {
     double two_pi_over_Lx, two_pi_over_Ly;
     double lp_a, lp_b, lp_c;  // low-pass band kx^2 lp_a + ky^2 lp_b <= lp_c (microstructure generator only)
     int max_newton, max_cg, max_pf;
+    int pf_precond;         // BCCG with the Fourier Helmholtz preconditioner
     int fracture, split, irrev;
 };
 

@@ -229,6 +229,7 @@ struct ModeK {
     T cx, cy, inv_n;
     int nx, ny;
     const Consts* kc;       // the problem constants (read only by rarely used multipliers)
+    T pre_a, pre_k;         // preconditioner (a_mean, 2 c ell^2), set by multipliers that need them
     ModeK() = default;
     __device__ __forceinline__ explicit ModeK(const Desc<T>& d)
         : cx(T(d.k.two_pi_over_Lx)), cy(T(d.k.two_pi_over_Ly)), inv_n(T(d.k.inv_n)), nx(d.nx), ny(d.ny), kc(&d.k) {}
@@ -460,11 +461,21 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
 
 // Column pass: CWE adjacent columns kx of the half spectrum, all NC planes.
 // OP::apply(d, kx, ky, vals[NC]) multiplies one mode (normalisation included).
+// column multipliers may read further per-problem constants into the ModeK (mode_prep)
+template <class OP, class = void> struct HasModePrep { static constexpr bool value = false; };
+template <class OP> struct HasModePrep<OP, decltype((void)&OP::template mode_prep<float>, void())> {
+    static constexpr bool value = true;
+};
+
 // skip test and mode constants of a column pass, evaluated once per block
 template <typename T, class OP>
 struct ColPrep {
     __device__ static bool skip(const Desc<T>& d) { return OP::skip(d); }
-    __device__ static ModeK<T> prep(const Desc<T>& d) { return ModeK<T>(d); }
+    __device__ static ModeK<T> prep(const Desc<T>& d) {
+        ModeK<T> m(d);
+        if constexpr (HasModePrep<OP>::value) OP::mode_prep(d, m);
+        return m;
+    }
 };
 
 template <typename T, int NY, int NC, class OP>

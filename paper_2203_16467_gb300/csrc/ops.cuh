@@ -383,7 +383,7 @@ struct FCopyOut {
 // v_con = phi_con(phi_n) - phi_n <= 0; v^0 = 0; r^0 = -b masked; p^0 = -r^0.
 template <typename T>
 struct FPfInit {
-    static constexpr int NR = 2;
+    static constexpr int NR = 3;
     struct Ctx { double g; int resc; double eb[3]; double eta_dt; int frozen; };
     __device__ static bool skip(const Desc<T>&) { return false; }
     __device__ static Ctx prep(const Desc<T>& d) {
@@ -428,6 +428,7 @@ struct FPfInit {
         d.flags[i] = (uint8_t)((at ? 1 : 0) | (active ? 2 : 0));
         acc[0].addp(r, r);
         acc[1].addp(b, b);
+        acc[2].add(a);
     }
     __device__ static void finalize(const Desc<T>& d, const double* tot) {
         Ctrl* c = d.ctrl;
@@ -445,6 +446,8 @@ struct FPfInit {
         c->pf_since_full = 0;
         c->pf_full_iters = 0;
         c->pf_rsel = 0;
+        c->pf_abar = tot[2] * k.inv_n;
+        c->pf_rz = 0.0;
         c->bar_count = 0;
         c->bar_abort = 0;
         c->pf_last_full = rn;
@@ -464,19 +467,21 @@ struct FPfInit {
 template <typename T> __device__ __forceinline__ T* pf_r(const Desc<T>& d, int sel) { return sel ? d.q[1] : d.th[1]; }
 
 template <typename T>
-struct FPfA1 {   // p = -r + beta p, zero on the active set; input p
+struct FPfA1 {   // p = -r + beta p (Algorithm 1) or p = -z + beta p (preconditioned), zero on the active set; input p
     static constexpr int NR = 0;
-    struct Ctx { T beta; int upd; const T* r; };
+    struct Ctx { T beta; int upd; int pre; const T* r; };
     __device__ static bool skip(const Desc<T>& d) {
+        if (d.k.pf_precond) return ldflag(&d.ctrl->pf_a);   // copied by the preconditioner's first pass
         int f = ldflag(&d.ctrl->pf_b);
         if (blockIdx.x == 0 && threadIdx.x == 0) d.ctrl->pf_a = f;
         return f;
     }
     __device__ static Ctx prep(const Desc<T>& d) {
         Ctx c;
-        c.upd = ldflag(&d.ctrl->pf_it) > 0;
+        c.pre = d.k.pf_precond;
+        c.upd = c.pre || ldflag(&d.ctrl->pf_it) > 0;
         c.beta = T(ldd(&d.ctrl->pf_beta));
-        c.r = pf_r(d, ldflag(&d.ctrl->pf_rsel));
+        c.r = c.pre ? d.q[2] : pf_r(d, ldflag(&d.ctrl->pf_rsel));   // z or r
         return c;
     }
     struct In { T p, r; uint8_t fl; };
@@ -495,6 +500,72 @@ struct FPfA1 {   // p = -r + beta p, zero on the active set; input p
         v[0] = p;
     }
     __device__ static void finalize(const Desc<T>&, const double*) {}
+};
+
+// Preconditioned variant (pff_params.pf_precondition): z = M^-1 r on the free set
+// with M = a_mean - 2 c ell^2 nabla^2_N, i.e. (a_mean + 2 c ell^2 |2 pi q|^2)^-1 per
+// Fourier mode -- the constant-coefficient part of J, inverted exactly by one FFT
+// pair.  Three passes: the residual forward along x, the mode multiplier along y,
+// the inverse along x with the masking and r.z, r_old.z -> beta (Polak-Ribiere in
+// the preconditioned inner product, r_old.z_old = -r_old.p_old after the step).
+template <typename T>
+struct FPfZIn {   // input r; first pass of an iteration: copies the stop flag
+    static constexpr int NR = 0;
+    struct Ctx { const T* r; };
+    __device__ static bool skip(const Desc<T>& d) {
+        int f = ldflag(&d.ctrl->pf_b);
+        if (blockIdx.x == 0 && threadIdx.x == 0) d.ctrl->pf_a = f;
+        return f;
+    }
+    __device__ static Ctx prep(const Desc<T>& d) { return Ctx{pf_r(d, ldflag(&d.ctrl->pf_rsel))}; }
+    struct In { T r; };
+    __device__ static In load(const Desc<T>&, const Ctx& c, size_t i) { return In{c.r[i]}; }
+    __device__ static void pixel(const Desc<T>&, const Ctx&, size_t, const In& a, T (&v)[1], Acc<T>*) { v[0] = a.r; }
+    __device__ static void finalize(const Desc<T>&, const double*) {}
+};
+
+struct FColPrecond {
+    template <typename T> __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
+    template <typename T> __device__ static void mode_prep(const Desc<T>& d, ModeK<T>& m) {
+        const double ab = ldd(&d.ctrl->pf_abar);
+        // a_mean >= eta/dt > 0 in Algorithm 4; a zero mean (eta/dt = 0 and no load) falls
+        // back to the smallest nonzero Laplacian eigenvalue scale
+        m.pre_a = T(ab > 0.0 ? ab : d.k.kappa * d.k.two_pi_over_Lx * d.k.two_pi_over_Lx);
+        m.pre_k = T(d.k.kappa);
+    }
+    template <typename T> __device__ static void apply(const ModeK<T>& m, int kx, int ky, typename CT<T>::t (&v)[1]) {
+        T qx = T(kx) * m.cx;
+        T qy = T(signed_k(ky, m.ny)) * m.cy;
+        T f = m.inv_n / (m.pre_a + m.pre_k * (qx * qx + qy * qy));
+        v[0].x *= f;
+        v[0].y *= f;
+    }
+};
+
+template <typename T>
+struct FPfZOut {   // z = M^-1 r masked to the free set (into q[2]); r.z, r_old.z -> beta
+    static constexpr int NR = 2;
+    struct Ctx { const T* r; const T* ro; };
+    __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
+    __device__ static Ctx prep(const Desc<T>& d) {
+        const int sel = ldflag(&d.ctrl->pf_rsel);
+        return Ctx{pf_r(d, sel), pf_r(d, sel ^ 1)};
+    }
+    struct In { T r, ro; uint8_t fl; };
+    __device__ static In load(const Desc<T>& d, const Ctx& c, size_t i) { return In{c.r[i], c.ro[i], d.flags[i]}; }
+    __device__ static void pixel(const Desc<T>& d, const Ctx&, size_t i, const In& a, T (&v)[1], Acc<T>* acc) {
+        const T z = (a.fl & 2) ? T(0) : v[0];
+        d.q[2][i] = z;
+        acc[0].addp(z, a.r);
+        acc[1].addp(z, a.ro);
+    }
+    __device__ static void finalize(const Desc<T>& d, const double* tot) {
+        Ctrl* c = d.ctrl;
+        const double den = c->pf_rz;
+        // the first iteration has no previous residual (beta = 0, p = -z)
+        c->pf_beta = (c->pf_it > 0 && den != 0.0) ? (tot[0] - tot[1]) / den : 0.0;
+        c->pf_rz = tot[0];
+    }
 };
 
 struct FColLapPF {
@@ -535,8 +606,10 @@ struct FPfA3 {   // J p; p.Jp, r.p -> alpha = -(r.p)/(p.Jp)
 // explicit residual kernel: beta, ||r||, active count and the stopping decision.
 template <typename T>
 __device__ __forceinline__ void pf_finish(const Desc<T>& d, Ctrl* c, double rr, double rro, double nact, bool full) {
-    double den = -c->pf_rp;   // = alpha p.Jp
-    c->pf_beta = den != 0.0 ? (rr - rro) / den : 0.0;
+    if (!d.k.pf_precond) {   // (the preconditioned variant takes beta from the z pass)
+        double den = -c->pf_rp;   // = alpha p.Jp
+        c->pf_beta = den != 0.0 ? (rr - rro) / den : 0.0;
+    }
     c->pf_rr = rr;
     c->pf_it += 1;
     c->n_active = (int)nact;
@@ -638,14 +711,15 @@ struct FColLapPFFull {
 template <typename T>
 struct FPfB3 {   // explicit R = J v - b, active set {bound and R > 0}, beta, convergence (only when pf_full)
     static constexpr int NR = 3;
-    struct Ctx { T kappa; double kd; T* r; };
+    struct Ctx { T kappa; double kd; const T* ro; T* rn; };
     __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a) || !ldflag(&d.ctrl->pf_full); }
     __device__ static Ctx prep(const Desc<T>& d) {
-        return Ctx{T(d.k.kappa), d.k.kappa, pf_r(d, ldflag(&d.ctrl->pf_rsel))};
+        const int sel = ldflag(&d.ctrl->pf_rsel);
+        return Ctx{T(d.k.kappa), d.k.kappa, pf_r(d, sel), pf_r(d, sel ^ 1)};
     }
     struct In { T ro, x, a, b; uint8_t fl; };
     __device__ static In load(const Desc<T>& d, const Ctx& c, size_t i) {
-        return In{c.r[i], d.th[0][i], d.r[0][i], d.r[1][i], d.flags[i]};
+        return In{c.ro[i], d.th[0][i], d.r[0][i], d.r[1][i], d.flags[i]};
     }
     __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, const In& in, T (&v)[1], Acc<T>* acc) {
         const T ro = in.ro, x = in.x, a = in.a, b = in.b, kl = c.kappa * v[0];
@@ -666,13 +740,14 @@ struct FPfB3 {   // explicit R = J v - b, active set {bound and R > 0}, beta, co
         }
         const bool active = at && pos;
         if (active) rn = T(0);
-        c.r[i] = rn;
+        c.rn[i] = rn;   // beside the previous residual (kept for the preconditioned beta)
         d.flags[i] = (uint8_t)((at ? 1 : 0) | (active ? 2 : 0));
         acc[0].addp(rn, rn);
         acc[1].addp(rn, ro);
         acc[2].add(active ? T(1) : T(0));
     }
     __device__ static void finalize(const Desc<T>& d, const double* tot) {
+        d.ctrl->pf_rsel ^= 1;
         pf_finish(d, d.ctrl, tot[0], tot[1], tot[2], true);
     }
 };

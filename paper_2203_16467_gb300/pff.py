@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
                 ("crack_set_threshold", ctypes.c_double), ("d_eps_bar", ctypes.c_double * 3),
                 ("compute_energies", ctypes.c_int), ("evolution", ctypes.c_int), ("tol_am", ctypes.c_double),
                 ("am_max_inner", ctypes.c_int), ("dt_min", ctypes.c_double), ("dt_max", ctypes.c_double),
-                ("dphi_max", ctypes.c_double)]
+                ("dphi_max", ctypes.c_double), ("pf_precondition", ctypes.c_int)]
 
 
 class StepReport(ctypes.Structure):
@@ -216,6 +216,9 @@ def create_problem(nx, ny, precision=MIXED, stream=None):
 
 def destroy_problem(h):
     return _check(lib.pff_destroy_problem(h))
+
+
+_PARAM_FIELDS = frozenset(f[0] for f in Params._fields_)
 
 
 def set_params(h, p):
@@ -440,8 +443,10 @@ class Problem:
             if k == "d_eps_bar":
                 for j in range(3):
                     p.d_eps_bar[j] = float(v[j])
-            else:
+            elif k in _PARAM_FIELDS:
                 setattr(p, k, v)
+            else:
+                raise TypeError(f"unknown parameter {k!r}")
         set_params(self.h, p)
 
     def set_model(self, fracture, split, irreversibility):
