@@ -337,10 +337,12 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     C* tws = buf + Cfg::NSEQ * Cfg::SP;
-    stage_row_twiddles<T, NX, NC>(d, tws);
     pdl_enter();
     typename F::Ctx ctx;
-    if (block_prep<F>(d, ctx)) { cp_async_wait_all(); return; }
+    if (block_prep<F>(d, ctx)) return;
+    // twiddles are needed only after the pixel phase: staged after the skip test,
+    // so that the blocks of a skipped problem return at once
+    stage_row_twiddles<T, NX, NC>(d, tws);
     const int y0 = blockIdx.x * Cfg::ROWS;
     constexpr int NRA = F::NR > 0 ? F::NR : 1;
     Acc<T> acc[NRA];
@@ -445,10 +447,10 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     C* tws = buf + Cfg::NSEQ * Cfg::SP;
-    stage_row_twiddles<T, NX, NC>(d, tws);
     pdl_enter();
     typename F::Ctx ctx;
-    if (block_prep<F>(d, ctx)) { cp_async_wait_all(); return; }
+    if (block_prep<F>(d, ctx)) return;
+    stage_row_twiddles<T, NX, NC>(d, tws);
     constexpr int NRA = F::NR > 0 ? F::NR : 1;
     Acc<T> acc[NRA];
     row_inv_item<T, NX, NC, F>(d, ctx, blockIdx.x * Cfg::ROWS, buf, tws, &acc[0]);
@@ -486,15 +488,15 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
     const Desc<T>& d = descs[blockIdx.y];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
+    pdl_enter();
+    ModeK<T> mk;
+    if (block_prep<ColPrep<T, OP>>(d, mk)) return;
     const C* tw = d.tw + NY;
     if constexpr (Cfg::TW_SMEM) {
         C* tws = buf + Cfg::NSEQ * SP;
         for (int t = threadIdx.x; t < NY; t += NT) cp_async<sizeof(C)>(&tws[pidx(t)], &d.tw[NY + t]);
         tw = tws;
     }
-    pdl_enter();
-    ModeK<T> mk;
-    if (block_prep<ColPrep<T, OP>>(d, mk)) { cp_async_wait_all(); return; }
     const int kx0 = blockIdx.x * CW;
     const size_t plane = (size_t)d.ny * d.wp;
     constexpr int TOT = NC * NY * CW;
@@ -624,6 +626,8 @@ __device__ __forceinline__ void col512_item(const Desc<T>& d, const ModeK<T>& mk
     for (int c = 0; c < NC; ++c)
 #pragma unroll
         for (int m = 0; m < 8; ++m) u[c][m] = d.S[c * plane + (size_t)(t + 64 * m) * d.wp + kx];
+    cp_async_wait_all();   // staged twiddles (a no-op when the caller has waited already)
+    __syncthreads();
     fft512_reg<T, false, NC, CW>(u, t, t, xb + j * COL512_XS, tws);
     const int k1 = t >> 3, cc = t & 7;
 #pragma unroll
@@ -650,12 +654,10 @@ __global__ void __launch_bounds__(64 * COL512_CW) k_col512(const Desc<T>* __rest
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tws = reinterpret_cast<C*>(smem_raw);
     C* xb = tws + padded_len(512);
-    stage_col512_twiddles<T>(d, tws);
     pdl_enter();
     ModeK<T> mk;
-    if (block_prep<ColPrep<T, OP>>(d, mk)) { cp_async_wait_all(); return; }
-    cp_async_wait_all();
-    __syncthreads();
+    if (block_prep<ColPrep<T, OP>>(d, mk)) return;
+    stage_col512_twiddles<T>(d, tws);   // waited for inside the item, after its loads are issued
     col512_item<T, NC, OP, COL512_CW>(d, mk, blockIdx.x * COL512_CW, xb, tws);
 }
 
