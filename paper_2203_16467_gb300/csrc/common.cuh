@@ -339,20 +339,30 @@ template <typename T> __device__ __forceinline__ T hv(T x) { return x > T(0) ? T
 // sqrt(d^2 + xy^2), u = d/rad, w = xy/rad:
 //   P1 = 1/2 [[1+u, w], [w, 1-u]],  P2 = I - P1,  S = [[-w, u], [u, w]]
 // (S = n1 n2^T + n2 n1^T).  deg marks coincident principal strains.
+// irad = 1/rad when not deg.  FP32 takes rad and 1/rad from one reciprocal
+// square root (rsqrtf, 2 ulp) instead of a correctly rounded root and division.
 template <typename T>
 struct Eig2 {
-    T e1, e2, u, w, tr;
+    T e1, e2, u, w, tr, irad;
     bool deg;
     __device__ __forceinline__ Eig2(T xx, T yy, T xy) {
         tr = xx + yy;
         T d = T(0.5) * (xx - yy);
-        T rad = sqrt(d * d + xy * xy);
+        T s2 = d * d + xy * xy;
+        T rad;
+        if constexpr (sizeof(T) == 4) {
+            irad = s2 > T(0) ? rsqrtf(s2) : T(0);
+            rad = s2 * irad;
+        } else {
+            rad = sqrt(s2);
+            irad = rad > T(0) ? T(1) / rad : T(0);
+        }
         e1 = T(0.5) * tr + rad;
         e2 = T(0.5) * tr - rad;
         T scale = fmax(fabs(e1), fabs(e2));
         deg = !(T(2) * rad > T(1e-12) * scale) || rad == T(0);
         if (deg) { u = T(1); w = T(0); }
-        else { T inv = T(1) / rad; u = d * inv; w = xy * inv; }
+        else { u = d * irad; w = xy * irad; }
     }
 };
 
@@ -480,7 +490,12 @@ __device__ __forceinline__ void tangent(int split, T xx, T yy, T xy, T hphi, T l
             dxx = H * pxx; dyy = H * pyy; dxy = H * pxy;
         } else {
             T H1 = hv(g.e1), H2 = hv(g.e2);
-            T g12 = (rp(g.e1) - rp(g.e2)) / (g.e1 - g.e2);
+            // divided difference (<e1>_+ - <e2>_+)/(e1 - e2): H(e1) when e1 and e2 have
+            // the same sign (exactly, as the quotient of equal values), e1 / (2 rad)
+            // when they straddle zero (no cancellation there); FP32 avoids the division
+            T g12;
+            if constexpr (sizeof(T) == 4) g12 = (g.e1 > T(0) && g.e2 < T(0)) ? g.e1 * (T(0.5) * g.irad) : H1;
+            else g12 = (rp(g.e1) - rp(g.e2)) / (g.e1 - g.e2);
             T u = g.u, w = g.w;
             T P1p = T(0.5) * ((T(1) + u) * pxx + (T(1) - u) * pyy + T(2) * w * pxy);
             T P2p = T(0.5) * ((T(1) - u) * pxx + (T(1) + u) * pyy - T(2) * w * pxy);

@@ -678,7 +678,9 @@ __device__ __forceinline__ void gamma_apply(const ModeK<T>& m, int kx, int ky, t
     }
     T qx = T(kx) * m.cx;
     T qy = T(signed_k(ky, m.ny)) * m.cy;
-    T inv = T(1) / sqrt(qx * qx + qy * qy);
+    T inv;
+    if constexpr (sizeof(T) == 4) inv = rsqrtf(qx * qx + qy * qy);   // 2 ulp, one instruction
+    else inv = T(1) / sqrt(qx * qx + qy * qy);
     T n1 = qx * inv, n2 = qy * inv;
     T sc = m.inv_n;
     C a = v[0], b = v[1], c = v[2];
