@@ -91,8 +91,10 @@ static void timing_collect() {
     g_tm.pending.swap(keep);
 }
 
+void note_launch_error(cudaError_t e);
+// Opt a kernel in to its dynamic shared memory when static plus dynamic shared
+// memory exceeds the 48 KB available without the attribute.
 bool smem_optin(const void* fn, size_t smem) {
-    if (smem <= 48 * 1024) return true;
     int dev = 0;
     cudaGetDevice(&dev);
     static std::mutex mu;
@@ -100,9 +102,26 @@ bool smem_optin(const void* fn, size_t smem) {
     std::lock_guard<std::mutex> g(mu);
     unsigned long long& m = done[fn];
     if (m & (1ull << (dev & 63))) return true;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e == cudaSuccess && fa.sharedSizeBytes + smem > 48 * 1024)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) m |= 1ull << (dev & 63);
+    else note_launch_error(e);
     return e == cudaSuccess;
+}
+
+// The first failed launch of this host thread, reported by the next poll of the
+// group (kernel launches return configuration errors only to their caller).
+static thread_local cudaError_t t_launch_err = cudaSuccess;
+void note_launch_error(cudaError_t e) {
+    if (t_launch_err == cudaSuccess) t_launch_err = e;
+}
+static cudaError_t take_launch_error() {
+    cudaError_t e = t_launch_err;
+    t_launch_err = cudaSuccess;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e;
 }
 
 // Keeps the stream busy for about ns nanoseconds (bounded by time and by an
@@ -564,7 +583,7 @@ static void run_chunk(int kind, Group& g, bool& warmed) {
             cudaGraphDestroy(graph);
         }
         if (e != cudaSuccess) {
-            cudaGetLastError();
+            take_launch_error();   // the capture failed; the chunk is launched directly instead
             gc->exec[kind] = nullptr;
             gc->failed[kind] = true;
             chunk_direct<T>(kind, g);
@@ -578,8 +597,10 @@ static void run_chunk(int kind, Group& g, bool& warmed) {
 template <typename T>
 static int poll(Group& g, bool ctrl_too, pff_problem* eh) {
     const Desc<T>* d = (const Desc<T>*)g.d_desc;
+    cudaError_t e = take_launch_error();
+    if (e != cudaSuccess) return cuda_fail(eh, e, "kernel launch");
     launch_gather<T>(d, g.np, g.d_flags, ctrl_too ? (void*)g.d_ctrl : nullptr, g.st);
-    cudaError_t e = cudaMemcpyAsync(g.h_flags, g.d_flags, sizeof(int) * g.np, cudaMemcpyDeviceToHost, g.st);
+    e = cudaMemcpyAsync(g.h_flags, g.d_flags, sizeof(int) * g.np, cudaMemcpyDeviceToHost, g.st);
     if (e == cudaSuccess && ctrl_too)
         e = cudaMemcpyAsync(g.h_ctrl, g.d_ctrl, sizeof(Ctrl) * g.np, cudaMemcpyDeviceToHost, g.st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g.st);
@@ -673,7 +694,7 @@ static int step_group(Group& g, int max_cg, int max_pf, int max_newton, bool ene
         launch_col<T>(CO_LAP_PLAIN, g.nx, g.ny, g.wp, d, g.np, g.st);
         launch_row_inv<T>(RI_ENERGY, g.nx, g.ny, d, g.np, g.st);
     }
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = take_launch_error();
     if (e != cudaSuccess) return cuda_fail(eh, e, "kernel launch");
     return poll<T>(g, true, eh);
 }
@@ -740,7 +761,7 @@ static void elem(pff_problem* h, int op) {
     else launch_elem<float>(op, h->nx, h->ny, (const Desc<float>*)h->d_desc, 1, h->st);
 }
 static int sync(pff_problem* h, const char* where) {
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = take_launch_error();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     return e == cudaSuccess ? 0 : cuda_fail(h, e, where);
 }

@@ -248,64 +248,65 @@ template <> struct RedOps<DF> {
     __device__ static double total(DF v) { return (double)v.hi + (double)v.lo; }
 };
 
+// Block reduction in a fixed order: every thread stores its NR values in shared
+// memory, then warp w reduces values k = w, w + NW, ... (lane l adds entries
+// l, l + 32, ... in order, then a shuffle tree), so that each value costs one
+// warp's tree instead of a tree in every warp.  res is valid in thread 0.
+template <int NR, int NT, typename V>
+__device__ __forceinline__ void block_reduce(const V (&v)[NR], V (&res)[NR]) {
+    using O = RedOps<V>;
+    constexpr int NW = NT / 32;
+    __shared__ V sh[NR][NT];
+    __shared__ V shr[NR];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) sh[k][threadIdx.x] = v[k];
+    __syncthreads();
+    for (int k = warp; k < NR; k += NW) {
+        V x = sh[k][lane];
+#pragma unroll
+        for (int j = 1; j < NW; ++j) x = O::add(x, sh[k][lane + 32 * j]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = O::add(x, O::shfl(x, o));
+        if (lane == 0) shr[k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) res[k] = shr[k];
+    }
+}
+
 template <int NR, int NT, typename V>
 __device__ __forceinline__ bool reduce_grid(V (&v)[NR], double* part, unsigned* counter, int nblocks,
                                             double (&tot)[NR]) {
     using O = RedOps<V>;
-    constexpr int NW = NT / 32;
-    __shared__ V sh[NR][NW];
     __shared__ int s_last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    V bs[NR];
+    block_reduce<NR, NT>(v, bs);
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < NR; ++k) {
-        V x = v[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x = O::add(x, O::shfl(x, o));
-        if (lane == 0) sh[k][warp] = x;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        V x[NR];
-#pragma unroll
-        for (int k = 0; k < NR; ++k) x[k] = lane < NW ? sh[k][lane] : O::zero();
-#pragma unroll
-        for (int o = NW / 2; o > 0; o >>= 1)
-#pragma unroll
-            for (int k = 0; k < NR; ++k) x[k] = O::add(x[k], O::shfl(x[k], o));
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < NR; ++k) O::store(part, (size_t)blockIdx.x * NR + k, x[k]);
-            __threadfence();
-            unsigned t = atomicAdd(counter, 1u);
-            s_last = (t == (unsigned)(nblocks - 1));
-        }
+        for (int k = 0; k < NR; ++k) O::store(part, (size_t)blockIdx.x * NR + k, bs[k]);
+        __threadfence();
+        unsigned t = atomicAdd(counter, 1u);
+        s_last = (t == (unsigned)(nblocks - 1));
     }
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
     // fixed-order sum of the partials: thread t takes blocks t, t+NT, ... in order
+    V x[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
-        V x = O::zero();
-        for (int b = threadIdx.x; b < nblocks; b += NT) x = O::add(x, O::load(part, (size_t)b * NR + k));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x = O::add(x, O::shfl(x, o));
-        if (lane == 0) sh[k][warp] = x;
+        x[k] = O::zero();
+        for (int b = threadIdx.x; b < nblocks; b += NT) x[k] = O::add(x[k], O::load(part, (size_t)b * NR + k));
     }
-    __syncthreads();
-    if (warp == 0) {
-        V x[NR];
+    V tt[NR];
+    block_reduce<NR, NT>(x, tt);
+    if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NR; ++k) x[k] = lane < NW ? sh[k][lane] : O::zero();
-#pragma unroll
-        for (int o = NW / 2; o > 0; o >>= 1)
-#pragma unroll
-            for (int k = 0; k < NR; ++k) x[k] = O::add(x[k], O::shfl(x[k], o));
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < NR; ++k) tot[k] = O::total(x[k]);
-            *counter = 0u;
-        }
+        for (int k = 0; k < NR; ++k) tot[k] = O::total(tt[k]);
+        *counter = 0u;
     }
     return true;
 }

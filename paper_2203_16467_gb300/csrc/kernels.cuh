@@ -240,6 +240,7 @@ struct FFlagsField {   // active flag -> p[1]
 // ---------------------------------------------------------------------------
 // launch helpers
 void count_launch();
+void note_launch_error(cudaError_t e);   // reported by the next poll of this host thread
 bool pdl_on();   // launch the operator kernels with programmatic stream serialization
 
 // Launch of a kernel that begins with pdl_enter() (row, column and elementwise
@@ -257,7 +258,8 @@ inline void launch_pdl(void (*fn)(P...), dim3 grid, dim3 block, size_t smem, cud
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = (sizeof(T) == 4 && pdl_on()) ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, fn, args...);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, fn, args...);
+    if (e != cudaSuccess) note_launch_error(e);
 }
 bool smem_optin(const void* fn, size_t smem);
 // optional per-kernel-class event timing (see pff_timing_enable); key = family * 16 + op
