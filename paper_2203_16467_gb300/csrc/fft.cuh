@@ -278,18 +278,18 @@ __device__ __forceinline__ void row_fwd_pixels(const Desc<T>& d, const typename 
                 T v[NC];
                 F::pixel(d, ctx, (size_t)(y0 + row) * NX + x, in[j], v, acc);
 #pragma unroll
-                for (int c = 0; c < NC; ++c) rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)] = v[c];
+                for (int c = 0; c < NC; ++c) rb[(c * ROWS + row) * 2 * SP + ridx(x)] = v[c];
             }
         }
     } else {
 #pragma unroll 4
         for (int t = threadIdx.x; t < ROWS * NX; t += NT) {
             const int row = t / NX, x = t % NX;
-            const size_t pix = (size_t)(y0 + row) * NX + x;
+            const size_t pix = (unsigned)(y0 + row) * NX + x;
             T v[NC];
             pixel_one<F>(d, ctx, pix, v, acc);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)] = v[c];
+            for (int c = 0; c < NC; ++c) rb[(c * ROWS + row) * 2 * SP + ridx(x)] = v[c];
         }
     }
 }
@@ -304,7 +304,7 @@ __device__ __forceinline__ void row_fwd_fft_store(const Desc<T>& d, int y0, type
     fft_smem<T, M, Cfg::NSEQ, SP, NT, false, true>(buf, tws);
     // real-to-complex post-processing: X[k] = Xe[k] + W_N^k Xo[k], k = 0..M
     const C* twN = tws + Cfg::TWF;
-    const size_t plane = (size_t)d.ny * d.wp;
+    const unsigned plane = (unsigned)d.ny * d.wp;   // 32-bit indices: < 2^32 elements
     for (int t = threadIdx.x; t < Cfg::NSEQ * (M + 1); t += NT) {
         const int s = t / (M + 1), k = t % (M + 1);
         const int c = s / ROWS, row = s % ROWS;
@@ -314,7 +314,7 @@ __device__ __forceinline__ void row_fwd_fft_store(const Desc<T>& d, int y0, type
         C e = C{T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y + zm.y)};
         C o = C{T(0.5) * (zk.y - zm.y), T(-0.5) * (zk.x - zm.x)};
         C X = cadd(e, cmul(twN[k], o));
-        d.S[c * plane + (size_t)(y0 + row) * d.wp + k] = X;
+        d.S[c * plane + (unsigned)(y0 + row) * d.wp + k] = X;
     }
 }
 
@@ -376,11 +376,11 @@ __device__ __forceinline__ void row_inv_item(const Desc<T>& d, const typename F:
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             const int t = threadIdx.x + j * NT;
-            in[j] = F::load(d, ctx, (size_t)(y0 + t / NX) * NX + t % NX);
+            in[j] = F::load(d, ctx, (size_t)((unsigned)(y0 + t / NX) * NX + t % NX));
         }
     }
     const C* twN = tws + Cfg::TWF;
-    const size_t plane = (size_t)d.ny * d.wp;
+    const unsigned plane = (unsigned)d.ny * d.wp;   // 32-bit indices: < 2^32 elements
     // complex-to-real pre-processing: Z[k] = A + i B,
     //   A = X[k] + conj(X[M-k]),  B = (X[k] - conj(X[M-k])) e^{+2 pi i k/N}
     // (imaginary parts of X[0] and X[M] are dropped, as for a real inverse).
@@ -388,7 +388,7 @@ __device__ __forceinline__ void row_inv_item(const Desc<T>& d, const typename F:
     for (int t = threadIdx.x; t < Cfg::NSEQ * (M + 1); t += NT) {
         const int s = t / (M + 1), k = t % (M + 1);
         const int c = s / ROWS, row = s % ROWS;
-        cp_async<sizeof(C)>(&buf[s * SP + pidx(k)], &d.S[c * plane + (size_t)(y0 + row) * d.wp + k]);
+        cp_async<sizeof(C)>(&buf[s * SP + pidx(k)], &d.S[c * plane + (unsigned)(y0 + row) * d.wp + k]);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -421,18 +421,18 @@ __device__ __forceinline__ void row_inv_item(const Desc<T>& d, const typename F:
             const int row = t / NX, x = t % NX;
             T v[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) v[c] = rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)];
-            F::pixel(d, ctx, (size_t)(y0 + row) * NX + x, in[j], v, acc);
+            for (int c = 0; c < NC; ++c) v[c] = rb[(c * ROWS + row) * 2 * SP + ridx(x)];
+            F::pixel(d, ctx, (size_t)((unsigned)(y0 + row) * NX + x), in[j], v, acc);
         }
     } else {
         (void)in;
 #pragma unroll 4
         for (int t = threadIdx.x; t < ROWS * NX; t += NT) {
             const int row = t / NX, x = t % NX;
-            const size_t pix = (size_t)(y0 + row) * NX + x;
+            const size_t pix = (unsigned)(y0 + row) * NX + x;
             T v[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) v[c] = rb[(size_t)(c * ROWS + row) * 2 * SP + ridx(x)];
+            for (int c = 0; c < NC; ++c) v[c] = rb[(c * ROWS + row) * 2 * SP + ridx(x)];
             pixel_one<F>(d, ctx, pix, v, acc);
         }
     }
@@ -498,11 +498,11 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
         tw = tws;
     }
     const int kx0 = blockIdx.x * CW;
-    const size_t plane = (size_t)d.ny * d.wp;
+    const unsigned plane = (unsigned)d.ny * d.wp;   // 32-bit indices: < 2^32 elements
     constexpr int TOT = NC * NY * CW;
     for (int t = threadIdx.x; t < TOT; t += NT) {
         const int j = t % CW, ky = (t / CW) % NY, c = t / (CW * NY);
-        cp_async<sizeof(C)>(&buf[(c * CW + j) * SP + pidx(ky)], &d.S[c * plane + (size_t)ky * d.wp + kx0 + j]);
+        cp_async<sizeof(C)>(&buf[(c * CW + j) * SP + pidx(ky)], &d.S[c * plane + (unsigned)ky * d.wp + kx0 + j]);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
 #pragma unroll 4
     for (int t = threadIdx.x; t < TOT; t += NT) {
         const int j = t % CW, ky = (t / CW) % NY, c = t / (CW * NY);
-        d.S[c * plane + (size_t)ky * d.wp + kx0 + j] = buf[(c * CW + j) * SP + pidx(ky)];
+        d.S[c * plane + (unsigned)ky * d.wp + kx0 + j] = buf[(c * CW + j) * SP + pidx(ky)];
     }
 }
 
@@ -620,12 +620,12 @@ __device__ __forceinline__ void col512_item(const Desc<T>& d, const ModeK<T>& mk
     using C = typename CT<T>::t;
     const int j = threadIdx.x % CW, t = threadIdx.x / CW;
     const int kx = kx0 + j;
-    const size_t plane = (size_t)d.ny * d.wp;
+    const unsigned plane = (unsigned)d.ny * d.wp;   // 32-bit indices: < 2^32 elements
     C u[NC][8];
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int m = 0; m < 8; ++m) u[c][m] = d.S[c * plane + (size_t)(t + 64 * m) * d.wp + kx];
+        for (int m = 0; m < 8; ++m) u[c][m] = d.S[c * plane + (unsigned)(t + 64 * m) * d.wp + kx];
     cp_async_wait_all();   // staged twiddles (a no-op when the caller has waited already)
     __syncthreads();
     fft512_reg<T, false, NC, CW>(u, t, t, xb + j * COL512_XS, tws);
@@ -644,7 +644,7 @@ __device__ __forceinline__ void col512_item(const Desc<T>& d, const ModeK<T>& mk
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int e = 0; e < 8; ++e) d.S[c * plane + (size_t)(tp + 64 * e) * d.wp + kx] = u[c][e];
+        for (int e = 0; e < 8; ++e) d.S[c * plane + (unsigned)(tp + 64 * e) * d.wp + kx] = u[c][e];
 }
 
 template <typename T, int NC, class OP>

@@ -12,21 +12,22 @@ constexpr int EL_NT = 256;
 // launch's blocks (accumulating F's reductions in acc).
 template <typename T, class F>
 __device__ __forceinline__ void elem_items(const Desc<T>& d, const typename F::Ctx& ctx, Acc<T>* acc) {
-    const size_t n = (size_t)d.nx * d.ny;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    // 32-bit pixel indices (grids have fewer than 2^32 pixels), widened at the access
+    const unsigned n = (unsigned)d.nx * d.ny;
+    const unsigned stride = gridDim.x * blockDim.x;
     if constexpr (HasIn<F>::value) {
         constexpr int U = 4;   // pixels whose loads are in flight together
-        for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += U * stride) {
+        for (unsigned base = blockIdx.x * blockDim.x + threadIdx.x; base < n; base += U * stride) {
             typename F::In in[U];
 #pragma unroll
             for (int j = 0; j < U; ++j)
-                if (base + j * stride < n) in[j] = F::load(d, ctx, base + j * stride);
+                if (base + j * stride < n) in[j] = F::load(d, ctx, (size_t)(base + j * stride));
 #pragma unroll
             for (int j = 0; j < U; ++j)
-                if (base + j * stride < n) F::pixel(d, ctx, base + j * stride, in[j], acc);
+                if (base + j * stride < n) F::pixel(d, ctx, (size_t)(base + j * stride), in[j], acc);
         }
     } else {
-        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) F::pixel(d, ctx, i, acc);
+        for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) F::pixel(d, ctx, (size_t)i, acc);
     }
 }
 
