@@ -427,6 +427,16 @@ def baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed):
                                        "3 load steps each after 1 warm-up step"}
     out["vs_plain_fp64_gpu"] = {"pixel_cg_iters_per_s": ((mech + bccg) * N * N / elapsed) / fp64_val,
                                 "load_steps_per_s": ours_steps / (f_steps / f_time)}
+    # the FFT kernels alone against cuFFT (timed comparator only)
+    try:
+        out["cufft_comparison"] = cufft_compare(pff, torch, stream)
+    except Exception as e:
+        out["cufft_comparison"] = {"error": str(e)[:200]}
+    # the dominant kernel class at 1, 2, 4 and 8 identical simulations per launch
+    try:
+        out["dominant_kernel_scaling"] = kernel_scaling(pff, torch, sp)
+    except Exception as e:
+        out["dominant_kernel_scaling"] = {"error": str(e)[:200]}
     # the opt-in Fourier-Helmholtz preconditioned BCCG against Algorithm 1, both from the
     # same start of the same eight variants, batched the way the timed region is
     try:
@@ -469,6 +479,90 @@ def baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed):
         out["cpu_baseline"] = {"value": None, "unit": "pixel-CG-iters/s", "cores": 1, "kind": "oracle",
                                "sample": f"failed: {e}"}
     return out
+
+
+def cufft_compare(pff, torch, stream, n=N, reps=200, warm=20):
+    """Laplacian of one n x n field through a real 2-D FFT round trip: this library's three
+    kernels (allocation-free C-ABI entries, FP32 and FP64) against torch.fft (cuFFT) with the
+    same multiplier -|2 pi q|^2, device-resident, CUDA events around reps calls on one stream."""
+    import ctypes
+    res = {"transform": f"real 2-D FFT, multiplier -|2 pi q|^2, inverse; {n}x{n}, one field",
+           "cufft": "torch.fft.rfft2 -> multiply -> torch.fft.irfft2 (cuFFT)", "reps": reps}
+    g = torch.Generator(device="cuda").manual_seed(7)
+    ky = torch.fft.fftfreq(n, d=1.0, device="cuda", dtype=torch.float64) * 2 * np.pi
+    kx = torch.fft.rfftfreq(n, d=1.0, device="cuda", dtype=torch.float64) * 2 * np.pi
+    mult64 = -(ky[:, None] ** 2 + kx[None, :] ** 2)
+    msg = ctypes.c_char_p()
+    for name, dt, fn in (("f32", torch.float32, pff.lib.pff_apply_laplacian_noalloc_f32),
+                         ("f64", torch.float64, pff.lib.pff_apply_laplacian_noalloc)):
+        x = torch.randn(n, n, generator=g, device="cuda", dtype=torch.float64).to(dt)
+        y = torch.empty_like(x)
+        mult = mult64.to(dt)
+        sp = ctypes.c_void_p(stream.cuda_stream)
+
+        def ours():
+            rc = fn(n, n, 1.0, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), sp, ctypes.byref(msg))
+            if rc:
+                raise RuntimeError(f"noalloc rc {rc}: {msg.value}")
+
+        def theirs():
+            return torch.fft.irfft2(torch.fft.rfft2(x) * mult, s=(n, n))
+
+        times = {}
+        with torch.cuda.stream(stream):
+            for tag, f in (("ours", ours), ("cufft", theirs)):
+                for _ in range(warm):
+                    f()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    f()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times[tag] = 1e3 * e0.elapsed_time(e1) / reps
+            ours()
+            ref = theirs()
+        torch.cuda.synchronize()
+        err = float((y.double() - ref.double()).abs().max() / ref.double().abs().max())
+        res[name] = {"ours_us": times["ours"], "cufft_us": times["cufft"], "speedup": times["cufft"] / times["ours"],
+                     "max_rel_diff": err}
+    return res
+
+
+def kernel_scaling(pff, torch, sp, key=(0, 1), variant=("AT1", "SPECTRAL", "CRACK_SET")):
+    """Average launch duration (CUDA events) and algorithmic GB/s of one kernel class when
+    every launch carries k identical simulations (all active in every launch), k = 1..8:
+    separates the fixed cost of a launch from the bandwidth of its work."""
+    peak, _ = hbm_peak()
+    bpp = bytes_per_px(4, N)[key]
+    rows = []
+    for k in (1, 2, 4, 8):
+        probs, _ = make_problems(pff, sp, 0, pff.MIXED, [variant] * k)
+        b = pff.create_batch(k, sum(pff.problem_bytes(N, N, pff.MIXED) for _ in probs), sp)
+        pff.batch_set_group_size(b, 0)
+        for p in probs:
+            assert pff.batch_admit(b, p.h) is not None
+        pff.batch_step(b, k, 2)
+        torch.cuda.synchronize()
+        pff.timing_reset()
+        pff.timing_enable(True)
+        out = pff.batch_step(b, k, 1)
+        pff.timing_enable(False)
+        ms, nl = pff.timing_read(*key)
+        pff.destroy_batch(b)
+        for p in probs:
+            p.close()
+        act = active_launches(out)[key]          # problem-launches that did work
+        work = act // k                           # launches with all k simulations working
+        gbs = act * bpp * N * N / (ms * 1e-3) / 1e9 if ms > 0 else None
+        rows.append({"simulations_per_launch": k, "launches": nl, "working_launches": work,
+                     "us_per_launch": 1e3 * ms / nl if nl else None, "achieved_GBs": gbs,
+                     "frac": gbs / peak if gbs else None})
+    return {"kernel": KERNEL_NAMES[key], "variant": "/".join(variant), "rows": rows,
+            "note": "one load step after two warm-up steps; the identical simulations work in the same "
+                    "launches; the skipped launches at the end of each 8-iteration chunk count against "
+                    "the time, as in the roofline figure"}
 
 
 def precond_compare(pff, torch, sp, warm=2, steps=6):

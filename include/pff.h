@@ -334,6 +334,11 @@ int pff_batch_autotune(pff_batch* b, const int* group_sizes, int n_candidates, i
 #define PFF_NOALLOC_MAX_N 512
 int pff_apply_laplacian_noalloc(int nx, int ny, double dx, const double* in_dev, double* out_dev,
                                 void* cuda_stream, const char** err_msg);
+/* The same in FP32 (the storage precision of PFF_MIXED problems): in_dev and
+ * out_dev are caller-owned FP32 device fields of nx*ny values; its own static
+ * scratch (about 1.1 MB), with the same sharing rule and errors as above. */
+int pff_apply_laplacian_noalloc_f32(int nx, int ny, double dx, const float* in_dev, float* out_dev,
+                                    void* cuda_stream, const char** err_msg);
 
 /* Library-wide counters: kernel launches issued since load (for benchmarks). */
 unsigned long long pff_kernel_launches(void);

@@ -117,7 +117,7 @@ static thread_local cudaError_t t_launch_err = cudaSuccess;
 void note_launch_error(cudaError_t e) {
     if (t_launch_err == cudaSuccess) t_launch_err = e;
 }
-static cudaError_t take_launch_error() {
+cudaError_t take_launch_error() {
     cudaError_t e = t_launch_err;
     t_launch_err = cudaSuccess;
     if (e == cudaSuccess) e = cudaGetLastError();

@@ -19,6 +19,7 @@
 #include "launch.h"
 
 namespace pff {
+cudaError_t take_launch_error();   // launches rejected by the runtime on this host thread (or the last error)
 namespace {
 
 constexpr int MT = 256;
@@ -198,7 +199,7 @@ int micro_generate(int nx, int ny, double dx, const pff_micro_params& mp, const 
             k_affine<<<nb, MT, 0, st>>>(src, E_dev, n, mp.E0 * mp.a, mp.E0);
             count_launch();
         }
-        e = cudaGetLastError();
+        e = take_launch_error();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cleanup();

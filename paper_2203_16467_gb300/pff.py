@@ -114,6 +114,8 @@ _SIGS = {
     "pff_set_persistent": (ctypes.c_int, [ctypes.c_int]),
     "pff_apply_laplacian_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
                                                    ctypes.POINTER(ctypes.c_char_p)]),
+    "pff_apply_laplacian_noalloc_f32": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
+                                                       ctypes.POINTER(ctypes.c_char_p)]),
     "pff_timing_reset": (ctypes.c_int, []),
     "pff_timing_read": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_ulonglong)]),
 }

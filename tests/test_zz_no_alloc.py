@@ -64,3 +64,35 @@ def test_noalloc_rejects_grids_beyond_the_limit(env):
     rc, msg = _call(pff, 48, 64, 1.0, src, dst, None)
     assert rc == pff.ERR_INVALID_ARG
     assert pff.kernel_launches() == launches   # nothing was launched
+
+
+@pytest.mark.parametrize("ny,nx", [(64, 64), (32, 128), (512, 512)])
+def test_noalloc_f32_matches_the_fp64_entry(env, ny, nx):
+    # the FP32 entry runs the mixed-precision kernels on caller-owned FP32 fields:
+    # within FP32 rounding of the FP64 entry's result on the same input
+    pff, torch = env
+    dx = 0.5
+    stream = torch.cuda.Stream()
+    rng = np.random.default_rng(3 * nx + ny)
+    g = rng.standard_normal((ny, nx))
+    src64 = torch.tensor(g, dtype=torch.float64, device="cuda")
+    dst64 = torch.empty_like(src64)
+    src32 = src64.float()
+    dst32 = torch.full((ny, nx), float("nan"), dtype=torch.float32, device="cuda")
+    msg = ctypes.c_char_p()
+    with torch.cuda.stream(stream):
+        rc, m = _call(pff, nx, ny, dx, src64, dst64, stream.cuda_stream)
+        assert rc == pff.OK, m
+        for _ in range(2):
+            rc = pff.lib.pff_apply_laplacian_noalloc_f32(nx, ny, dx, ctypes.c_void_p(src32.data_ptr()),
+                                                         ctypes.c_void_p(dst32.data_ptr()),
+                                                         ctypes.c_void_p(stream.cuda_stream), ctypes.byref(msg))
+            assert rc == pff.OK, msg.value
+    stream.synchronize()
+    ref = dst64.cpu().numpy()
+    out = dst32.double().cpu().numpy()
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < 2e-6
+    big = torch.zeros(16, dtype=torch.float32, device="cuda")
+    rc = pff.lib.pff_apply_laplacian_noalloc_f32(1024, 64, 1.0, ctypes.c_void_p(big.data_ptr()),
+                                                 ctypes.c_void_p(big.data_ptr()), None, ctypes.byref(msg))
+    assert rc == pff.ERR_INVALID_ARG and b"512" in msg.value
