@@ -189,6 +189,31 @@ def run_cpu_sample_subprocess(n_mech, n_bccg):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def run_cpu_sample_all_cores(n_mech, n_bccg, procs=None):
+    """The same oracle sample in one single-threaded process per host core, all started at one
+    time after their imports (independent simulations, as the GPU path batches them).  Returns
+    the mean per-iteration seconds of mechanics CG and BCCG under that contention, the process
+    count and the wall time of the slowest process."""
+    procs = procs or os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    t_start = time.time() + 8.0 + 0.05 * procs   # after every process has imported the oracle
+    code = (f"import sys, json, time; sys.path.insert(0, {ROOT!r}); import bench, oracle.mechanics; "
+            f"time.sleep(max(0.0, {t_start!r} - time.time())); "
+            f"r = bench.cpu_sample({n_mech}, {n_bccg}); print(json.dumps([time.time(), r]))")
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                           env=env) for _ in range(procs)]
+    ends, tms, tbs = [], [], []
+    for p in ps:
+        out, err = p.communicate(timeout=900)
+        if p.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        t_end, (tm, tb, _) = json.loads(out.strip().splitlines()[-1])
+        ends.append(t_end)
+        tms.append(tm)
+        tbs.append(tb)
+    return statistics.mean(tms), statistics.mean(tbs), procs, max(ends) - t_start
+
+
 # ------------------------------------------------------------------------- reference arm (oracle)
 def run_reference(args, rank):
     if rank != 0:
@@ -478,6 +503,16 @@ def baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed):
     except Exception as e:  # the baseline is reported, never required
         out["cpu_baseline"] = {"value": None, "unit": "pixel-CG-iters/s", "cores": 1, "kind": "oracle",
                                "sample": f"failed: {e}"}
+    try:
+        tm_p, tb_p, procs, wall = run_cpu_sample_all_cores(4, 40)
+        out["cpu_baseline"]["all_cores"] = {
+            "value": procs * (mech + bccg) * N * N / (mech * tm_p + bccg * tb_p), "unit": "pixel-CG-iters/s",
+            "cores": procs,
+            "sample": f"{procs} single-threaded oracle processes, each 4 mechanics CG + 40 BCCG iterations on its "
+                      f"own {N}x{N} grid, started together ({wall:.1f} s wall; {tm_p:.3f} s and {tb_p:.4f} s per "
+                      f"iteration under that contention), weighted by the timed region's iteration mix"}
+    except Exception as e:
+        out["cpu_baseline"]["all_cores"] = {"value": None, "sample": f"failed: {str(e)[:200]}"}
     return out
 
 
