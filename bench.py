@@ -45,6 +45,7 @@ WORKLOAD = "grid512_lc32_ell4_8variants_batched_mixed"
 GROUP_SIZE = 1
 L2_BYTES = 129e6
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0    # HBM3e nominal bandwidth of the part (context beside the measured peak)
 
 
 def eps_m():
@@ -415,6 +416,8 @@ def run_ours(args, rank, world, dev):
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                          "frac": (ach / peak) if ach else None, "peak_kind": peak_kind,
+                         "frac_of_nominal": (ach / NOMINAL_HBM_GBS) if ach else None,
+                         "nominal_peak": NOMINAL_HBM_GBS,
                          "traffic": measured_traffic(dom, kernels.get(dom, {}).get("alg_bytes_per_launch")),
                          "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled to this run's average launch)"},
             "kernels": kernels,
