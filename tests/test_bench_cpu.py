@@ -1,0 +1,33 @@
+"""The bench's roofline arithmetic on the CPU: the per-kernel algorithmic bytes per pixel add
+up to the per-iteration figures of the design notes (FP32 storage, 512-pixel rows), FP64 doubles
+every term, and the active-launch count follows the step reports (the explicit-residual chain
+works only in the iterations that evaluate J v explicitly)."""
+import pytest
+
+import bench
+
+
+def test_bytes_per_iteration_512():
+    b = bench.bytes_per_px(4, 512)
+    s = 8 * 257 / 512                                   # half-spectrum bytes per pixel per component
+    assert b[(0, 1)] == pytest.approx(26 * 4 + 3 * s)  # 116.05: the dominant kernel
+    cg = b[(0, 1)] + b[(2, 1)] + b[(1, 1)]
+    bccg = b[(0, 3)] + b[(2, 4)] + b[(1, 4)] + b[(3, 11)]
+    explicit = b[(0, 4)] + b[(2, 6)] + b[(1, 5)]
+    assert round(cg) == 188 and round(bccg) == 82 and round(explicit) == 46
+    b8 = bench.bytes_per_px(8, 512)
+    for k in b:
+        # FP64 doubles each value but the one-byte flag plane
+        flags = {(0, 3): 1, (3, 11): 1, (1, 5): 2}.get(k, 0)
+        assert b8[k] == pytest.approx(2 * (b[k] - flags) + flags)
+
+
+def test_active_launches_follow_the_reports():
+    reps = [[{"mech_cg_iters": 10, "newton_iters": 2, "bccg_iters": 7, "bccg_full_iters": 3}],
+            [{"mech_cg_iters": 4, "newton_iters": 1, "bccg_iters": 5, "bccg_full_iters": 1},
+             {"mech_cg_iters": 0, "newton_iters": 0, "bccg_iters": 0, "bccg_full_iters": 0}]]
+    a = bench.active_launches(reps)
+    assert a[(0, 1)] == 17 and a[(2, 1)] == 14 and a[(1, 1)] == 14
+    assert all(a[k] == 12 for k in ((0, 3), (2, 4), (1, 4), (3, 11)))
+    assert all(a[k] == 4 for k in ((0, 4), (2, 6), (1, 5)))
+    assert set(a) == set(bench.KERNEL_NAMES)
