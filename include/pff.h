@@ -30,6 +30,9 @@
  *     exception crosses the ABI.  pff_last_error(h) returns a message owned
  *     by the handle (valid until the next call on it).  A handle is not
  *     thread-safe; different handles may be used from different threads.
+ *   - PFF_ERR_CUDA covers CUDA runtime errors, including a kernel launch that
+ *     the runtime rejects (reported by the call that issued it, at its next
+ *     synchronisation point, never as a non-converging solve).
  *   - Grid sizes: nx and ny are powers of two from 16 to 2048.
  *   - The library needs an sm_103a GPU; there is no CPU fallback.
  */
