@@ -118,3 +118,86 @@ def test_time_dependent_step_halves_and_recovers_dt():
         dts.append(dt)
     assert max(dts) > min(dts)   # dt adapts
     assert np.all(st.phi >= -1e-12)
+
+
+# ---------------------------------------------------------------------------
+# energies() (Eq. Ff and the elastic energy of the contact model, Sec. 2.1)
+
+@pytest.mark.parametrize("fracture", [AT1, AT2])
+def test_energies_one_dimensional_crack_gives_Gc_per_length(fracture):
+    # Eq. Ff is normalised by c_w so that an ideal crack dissipates G_c per unit length
+    # (Sec. 2.1): the optimal 1-D profile (phase field held at 1 on one grid line, no
+    # elastic drive) evaluated by energies() tends to G_c * (crack length) as ell/dx grows.
+    # At the optimum the local and gradient parts contribute equally, so a wrong ell^2
+    # factor or a wrong c_w moves the result away from G_c.
+    ny, nx = 4, 256
+    out = []
+    for ell in (4.0, 8.0, 16.0):
+        par = Params(fracture=fracture, ell=ell, Gc=1.7, irreversibility=CRACK_SET, pf_tol=1e-13, pf_atol=1e-14)
+        phi = np.zeros((ny, nx))
+        psi = np.zeros((ny, nx))
+        b = pf.minus_F_phi(phi, psi, par)
+        vcon = pf.phi_con(phi, par) - phi
+        vcon[:, 0] = 1.0
+        v, _ = pf.bccg(lambda x: pf.J_apply(x, psi, par), b, vcon, par.pf_tol, par.pf_atol, 50000)
+        Fe, Ff = ev.energies(np.zeros((ny, nx, 2, 2)), v, np.ones((ny, nx)), par)
+        assert Fe == 0.0
+        out.append(Ff / (ny * par.dx) / par.Gc)
+    assert abs(out[2] - 1.0) < 0.02
+    assert abs(out[2] - 1.0) < abs(out[0] - 1.0) + 1e-12
+
+
+def test_energies_fracture_term_of_a_cosine_mode():
+    # a single Fourier mode phi = A cos(2 pi x / L) + B: sum phi^2 = N^2 (A^2/2 + B^2) and
+    # sum |grad phi|^2 = N^2 A^2 (2 pi / L)^2 / 2 (dx = 1), so for AT2 (f = phi^2)
+    # F_f = G_c/(2 ell) N^2 [A^2/2 + B^2 + ell^2 A^2 (2 pi/L)^2 / 2] exactly.
+    n, A, B, ell = 16, 0.3, 0.4, 2.5
+    par = Params(fracture=AT2, ell=ell, Gc=1.3)
+    x = np.arange(n)
+    phi = np.broadcast_to(A * np.cos(2 * np.pi * x / n) + B, (n, n)).copy()
+    _, Ff = ev.energies(np.zeros((n, n, 2, 2)), phi, np.ones((n, n)), par)
+    k = 2 * np.pi / n
+    exact = par.Gc / (2.0 * ell) * n * n * (A * A / 2 + B * B + ell ** 2 * A * A * k * k / 2)
+    assert Ff == pytest.approx(exact, rel=1e-12)
+
+
+@pytest.mark.parametrize("split", [ISOTROPIC, SPECTRAL, SPECTRAL_STRESSFREE])
+def test_energies_elastic_homogeneous_clapeyron(split):
+    # Homogeneous grid, phi = 0: the elastic energy is half the work of the mean stress on the
+    # applied strain, F_e = |Omega| sigma-bar : eps-bar / 2 (Clapeyron; psi is homogeneous of
+    # degree 2 in eps for every split), with sigma-bar from the stress of the contact model.
+    n, E0 = 8, 3.0
+    par = Params(split=split, dx=0.5)
+    E = np.full((n, n), E0)
+    lam, mu = cm.lame(E, par.nu)
+    for eb in (np.array([[0.01, 0.004], [0.004, -0.02]]), np.array([[-0.01, 0.0], [0.0, -0.03]]),
+               np.array([[0.02, 0.01], [0.01, 0.005]])):
+        eps = np.broadcast_to(eb, (n, n, 2, 2)).copy()
+        Fe, Ff = ev.energies(eps, np.zeros((n, n)), E, par)
+        sig = cm.stress(eps, np.zeros((n, n)), lam, mu, split).mean(axis=(0, 1))
+        area = (n * par.dx) ** 2
+        assert Fe == pytest.approx(0.5 * area * float(np.sum(sig * eb)), rel=1e-12)
+        assert Ff == 0.0
+
+
+def test_energies_elastic_of_broken_material_uses_the_contact_model():
+    # phi = 1 everywhere (h = 0): only psi_0^- of the contact model remains (Sec. 2.1, Sec. 4.2.1).
+    # Strain-spectral split: zero energy in tension, the full undamaged energy under
+    # all-compressive principal strains; the stress-free contact model keeps no energy at all.
+    n = 8
+    E = np.full((n, n), 2.0)
+    phi1, phi0 = np.ones((n, n)), np.zeros((n, n))
+    tension = np.broadcast_to(np.array([[0.01, 0.002], [0.002, 0.02]]), (n, n, 2, 2)).copy()
+    compression = -tension
+    sp = Params(split=SPECTRAL)
+    iso = Params(split=ISOTROPIC)
+    sf = Params(split=SPECTRAL_STRESSFREE)
+    assert ev.energies(tension, phi1, E, sp)[0] == 0.0
+    full = ev.energies(compression, phi0, E, iso)[0]
+    assert full > 0
+    assert ev.energies(compression, phi1, E, sp)[0] == pytest.approx(full, rel=1e-12)
+    assert ev.energies(compression, phi1, E, sf)[0] == 0.0
+    assert ev.energies(tension, phi1, E, iso)[0] == 0.0
+    # half-broken: h(1/2) = 1/4 of the isotropic energy
+    assert ev.energies(tension, 0.5 * phi1, E, iso)[0] == pytest.approx(0.25 * ev.energies(tension, phi0, E, iso)[0],
+                                                                        rel=1e-12)
