@@ -210,10 +210,12 @@ template <> struct Acc<float> {
 // fixed order and returns true with the totals in tot (valid in thread 0).
 // Deterministic: the summation tree depends only on the grid shape.
 //
-// FP32 problems reduce in double-float arithmetic (a value is an unevaluated
-// sum hi + lo of two floats, added with Knuth's two-sum), so that every level
-// stays on the FP32 pipe with about 44 significant bits and only the final
-// totals are converted to double; their partials are stored as float2.
+// FP32 problems: every product is formed exactly (fmaf split), each thread's
+// sum is a compensated float pair, and the block reduces the pairs in
+// double-float arithmetic (a value is an unevaluated sum hi + lo of two floats,
+// added with Knuth's two-sum; about 44 significant bits) so that the per-pixel
+// and per-thread work stays on the FP32 pipe; the block totals and the
+// cross-block sum are FP64 (reduce_grid).
 __device__ __forceinline__ DF df_add(DF a, DF b) {
     float s = a.hi + b.hi;
     float z = s - a.hi;
@@ -277,6 +279,10 @@ __device__ __forceinline__ void block_reduce(const V (&v)[NR], V (&res)[NR]) {
     }
 }
 
+// The cross-block stage is FP64 for both precisions: each block's total is stored
+// as one double (a double-float pair hi + lo converts exactly), and the last block
+// sums the partials in double.  Within a block an FP32 problem's values stay
+// double-float pairs (FP32 pipe); an FP64 problem's stay doubles.
 template <int NR, int NT, typename V>
 __device__ __forceinline__ bool reduce_grid(V (&v)[NR], double* part, unsigned* counter, int nblocks,
                                             double (&tot)[NR]) {
@@ -286,7 +292,7 @@ __device__ __forceinline__ bool reduce_grid(V (&v)[NR], double* part, unsigned* 
     block_reduce<NR, NT>(v, bs);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NR; ++k) O::store(part, (size_t)blockIdx.x * NR + k, bs[k]);
+        for (int k = 0; k < NR; ++k) __stcg(part + (size_t)blockIdx.x * NR + k, O::total(bs[k]));
         __threadfence();
         unsigned t = atomicAdd(counter, 1u);
         s_last = (t == (unsigned)(nblocks - 1));
@@ -294,18 +300,18 @@ __device__ __forceinline__ bool reduce_grid(V (&v)[NR], double* part, unsigned* 
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
-    // fixed-order sum of the partials: thread t takes blocks t, t+NT, ... in order
-    V x[NR];
+    // fixed-order FP64 sum of the partials: thread t takes blocks t, t+NT, ... in order
+    double x[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
-        x[k] = O::zero();
-        for (int b = threadIdx.x; b < nblocks; b += NT) x[k] = O::add(x[k], O::load(part, (size_t)b * NR + k));
+        x[k] = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += NT) x[k] += __ldcg(part + (size_t)b * NR + k);
     }
-    V tt[NR];
+    double tt[NR];
     block_reduce<NR, NT>(x, tt);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NR; ++k) tot[k] = O::total(tt[k]);
+        for (int k = 0; k < NR; ++k) tot[k] = tt[k];
         *counter = 0u;
     }
     return true;

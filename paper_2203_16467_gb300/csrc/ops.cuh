@@ -45,6 +45,11 @@ __device__ __forceinline__ void lame_at(const Desc<T>& d, size_t i, T& lam, T& m
 static __device__ __noinline__ bool resid_positive_fp64(float a, float x, double kappa, float l, float b) {
     return ((double)a * (double)x - kappa * (double)l - (double)b) > 0.0;
 }
+// FP64 sign of the recurrence residual R + alpha J p from the FP32 stored R and J p
+// and the FP64 step length (out of line for the same reason).
+static __device__ __noinline__ bool recur_positive_fp64(float R, double alpha, float Jp) {
+    return fma(alpha, (double)Jp, (double)R) > 0.0;
+}
 template <typename T> __device__ __forceinline__ T hdeg(T phi) { return (T(1) - phi) * (T(1) - phi); }
 
 // weighted (Frobenius) inner product of symmetric tensors stored (xx, yy, xy)
@@ -649,11 +654,12 @@ constexpr int PF_REFRESH = 32;
 template <typename T>
 struct FPfB1 {
     static constexpr int NR = 4;
-    struct Ctx { T alpha; const T* ro; T* rn; };
+    struct Ctx { T alpha; double alpha_d; const T* ro; T* rn; };
     __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
     __device__ static Ctx prep(const Desc<T>& d) {
         int sel = ldflag(&d.ctrl->pf_rsel);
-        return Ctx{T(ldd(&d.ctrl->pf_alpha)), pf_r(d, sel), pf_r(d, sel ^ 1)};
+        const double a = ldd(&d.ctrl->pf_alpha);
+        return Ctx{T(a), a, pf_r(d, sel), pf_r(d, sel ^ 1)};
     }
     struct In { T v, p, vc, R, Jp, ro; };
     __device__ static In load(const Desc<T>& d, const Ctx& c, size_t i) {
@@ -666,7 +672,20 @@ struct FPfB1 {
         const bool at = (x == a.vc);
         T rn = a.R + c.alpha * a.Jp;
         d.lap[i] = rn;
-        const bool active = at && rn > T(0);
+        bool pos = false;
+        if (at) {   // the sign only matters at the bound
+            if constexpr (sizeof(T) == 8) {
+                pos = rn > T(0);
+            } else {
+                // the FP32 recurrence differs from R + alpha_d J p (exact operands, FP64
+                // alpha) by at most 3 units of 2^-24 of |R| + |alpha J p|: beyond 4e-7 of
+                // that the FP32 sign is the FP64 sign, below it the sign is taken in FP64
+                T mag = fabs(a.R) + fabs(c.alpha * a.Jp);
+                if (fabs(rn) > T(4e-7) * mag) pos = rn > T(0);
+                else pos = recur_positive_fp64(a.R, c.alpha_d, a.Jp);
+            }
+        }
+        const bool active = at && pos;
         if (active) rn = T(0);
         c.rn[i] = rn;
         d.flags[i] = (uint8_t)((at ? 1 : 0) | (active ? 2 : 0));
@@ -678,9 +697,13 @@ struct FPfB1 {
         Ctrl* c = d.ctrl;
         const bool clamped = tot[0] > 0.0;
         if (clamped) c->pf_clamp_iters += 1;   // iterations in which the clamp changed v
-        const bool full = clamped || c->pf_force || c->pf_since_full + 1 >= PF_REFRESH;
+        // a recurrence residual that meets the tolerance is confirmed by the explicit
+        // J v - b of this same iteration, so that the solve stops at the iteration at
+        // which Algorithm 1's explicit residual first meets it
+        const bool rec_conv = sqrt(tot[1]) <= c->pf_target;
+        const bool full = clamped || rec_conv || c->pf_force || c->pf_since_full + 1 >= PF_REFRESH;
         c->pf_full = full;
-        c->pf_confirm = c->pf_force;
+        c->pf_confirm = rec_conv || c->pf_force;
         c->pf_force = 0;
         if (!full) {
             c->pf_rsel ^= 1;

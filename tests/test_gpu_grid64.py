@@ -89,14 +89,20 @@ def test_whole_run_crack_set(pff, gold, prec):
     reps = p.step_load(5000)
     assert reps[-1]["broken"]
     phi = p.get_fields(pff.FIELD_PHI)
-    # The crack tail of this workload is decided at the solver-tolerance level: the
-    # oracle's own runs at tolerances 1e-7 and 1e-10 end with a crack set that has
-    # IoU 0.977 against its run at 1e-8.  The comparison therefore uses the oracle's
-    # tolerance family (tests/golden/make_grid64_run.py --tolerance-family).
+    ious = {"tol1e-08": float(_iou(phi > 0.95, gold["phi_final"] > 0.95))}
     fam = np.load(FAMILY)
-    refs = {"tol1e-08": gold["phi_final"]}
-    refs.update({k.replace("phi_final_", ""): fam[k] for k in fam.files if k.startswith("phi_final")})
-    ious = {k: float(_iou(phi > 0.95, v > 0.95)) for k, v in refs.items()}
-    assert max(ious.values()) >= 0.98, (ious, len(reps), int(gold["n_steps"]))
+    ious.update({k.replace("phi_final_", ""): float(_iou(phi > 0.95, fam[k] > 0.95))
+                 for k in fam.files if k.startswith("phi_final")})
+    print("whole-run IoU", prec, ious, "steps", len(reps), "oracle steps", int(gold["n_steps"]))
+    if prec == 0:
+        # FP64 with the oracle's stopping rules: the crack set of the oracle's run at the
+        # workload's own tolerance (1e-8)
+        assert ious["tol1e-08"] >= 0.98, (ious, len(reps), int(gold["n_steps"]))
+    else:
+        # FP32 rounding perturbs every solve at about the level that separates the oracle's
+        # own runs at neighbouring tolerances, whose crack tails differ by three pixels
+        # (tests/golden/make_grid64_run.py --tolerance-family): the mixed run is compared
+        # with that family
+        assert max(ious.values()) >= 0.98, (ious, len(reps), int(gold["n_steps"]))
     assert phi.min() >= -1e-12 and phi.max() <= 1.0 + 1e-6
     p.close()

@@ -83,11 +83,25 @@ def test_phase_field_solve_parity(pff, prec, fracture, irr):
     err = rel_l2(phi, phi_ref)
     assert err < (1e-9 if prec == 0 else 1e-5), (err, rep["bccg_iters"], info["iters"])
     act = p.get_fields(pff.FIELD_ACTIVE) > 0.5
-    mism = int(np.sum(act != info["active"]))
     if prec == 0:
-        assert mism == 0
+        assert int(np.sum(act != info["active"])) == 0
     else:
-        assert mism <= max(2, act.size // 2000), mism
+        # The active set of Algorithm 1 is {v = v_con and r > 0}.  It is unique on every
+        # pixel that is strictly complementary at the oracle's solution: bound with r
+        # clearly positive (active), or clearly off the bound (free).  There the FP32/FP64
+        # path must agree exactly.  Pixels with both v - v_con and r within the mixed
+        # tolerance of zero may take either value (both are within the solve's accuracy);
+        # they must stay few, so that the exact comparison covers the field.
+        vcon = phasefield.phi_con(phi0, par) - phi0
+        b = phasefield.minus_F_phi(phi0, psi, par)
+        r = phasefield.J_apply(v_ref, psi, par) - b
+        bound = v_ref == vcon
+        sure_active = bound & (r > 1e-5 * np.abs(b).max())
+        sure_free = (v_ref - vcon) > 1e-5 * np.abs(v_ref).max()
+        decided = sure_active | sure_free
+        assert np.array_equal(act[decided], sure_active[decided]), int(np.sum(act[decided] != sure_active[decided]))
+        assert np.array_equal(sure_active, info["active"] & decided)
+        assert np.sum(~decided) <= act.size // 100, int(np.sum(~decided))
     assert phi.min() >= -1e-12
     p.close()
 
@@ -105,12 +119,25 @@ def test_load_steps_parity_32(pff, prec):
     nsteps = 40
     reps = p.step_load(nsteps)
     assert len(reps) == nsteps
+    rt = 1e-4 if prec else 1e-8
     for k in range(nsteps):
         r = ev.load_step(st, par)
         g = reps[k]
         np.testing.assert_allclose(g["eps_bar"], bar3(r["eps_bar"]), rtol=1e-5 if prec else 1e-9, atol=1e-12)
         assert g["incremented"] == r["incremented"]
         assert g["rescaled"] == r["rescaled"]
+        # per-step observables of Algorithm 4: mean stress, C-bar, the energies of Eq. Ff
+        # and of the contact model (Sec. 2.1), all against the oracle's on the same run
+        sb = bar3(r["sig_bar"])
+        scale = max(abs(x) for x in sb)
+        assert max(abs(a - b) for a, b in zip(g["sig_bar"], sb)) <= rt * scale, (k, g["sig_bar"], sb)
+        if np.isfinite(r["C_bar"]):
+            assert abs(g["C_bar"] - r["C_bar"]) <= rt * abs(r["C_bar"]), (k, g["C_bar"], r["C_bar"])
+        else:   # eps-bar = 0: C-bar undefined on both sides
+            assert not np.isfinite(g["C_bar"]), (k, g["C_bar"])
+        assert abs(g["F_e"] - r["F_e"]) <= rt * abs(r["F_e"]), (k, g["F_e"], r["F_e"])
+        assert abs(g["F_f"] - r["F_f"]) <= rt * max(abs(r["F_f"]), 1e-3), (k, g["F_f"], r["F_f"])
+    assert max(r["F_f"] for r in st.history) > 0.0   # the run reaches damage
     phi = p.get_fields(pff.FIELD_PHI)
     assert rel_l2(phi, st.phi) < (1e-7 if prec == 0 else 1e-4)
     p.close()
