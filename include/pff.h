@@ -58,9 +58,16 @@ enum {
 /* Storage / arithmetic precision of a problem. */
 enum {
     PFF_FP64 = 0,   /* all fields and arithmetic in FP64 */
-    PFF_MIXED = 1   /* fields and pointwise/FFT arithmetic in FP32; dot products,
-                       norms, scalars, the driving-force maximum and the
-                       phase-field bound decisions in FP64 */
+    PFF_MIXED = 1   /* fields and pointwise/FFT arithmetic in FP32.  Dot products
+                       and norms: each product formed exactly (FMA split), each
+                       thread's sum a compensated float pair, the pairs of a
+                       block summed in double-float arithmetic (about 44
+                       significant bits), block totals and the cross-block sum
+                       in FP64.  Solver scalars, the driving-force field, its
+                       maximum, x* and gamma in FP64.  Phase-field bound
+                       decisions (the sign of the residual at the bound): in FP64
+                       from the FP32 stored operands wherever the FP32 sign could
+                       differ from it. */
 };
 
 /* Local fracture energy f(phi) (Eq. fracturelocal): AT1 f = phi, c_w = 8/3;
@@ -380,6 +387,33 @@ int pff_set_pdl(int on);
  * host the launch the per-phase kernels run instead.  Synchronises the device.
  * No counterpart in the paper. */
 int pff_set_persistent(int on);
+
+/* Mechanics sub-problem of FP32 512 x 512 problems in one launch per solve
+ * (default on): one thread-block cluster of 16 CTAs per problem keeps the
+ * three-component half spectrum in distributed shared memory, so the column
+ * FFTs and the projection Gamma (Sec. 3.1.1) never move the spectrum through
+ * HBM, and the Newton rounds and CG iterations (Eqs. mech_newton,
+ * elasticity_newton_linear) run inside the launch with FP64 cluster
+ * reductions.  The CG step lengths use p.Ap = p.(C_m:p) and r.Ap = r.(C_m:p),
+ * exact for iterates in the range of the projection, and q.q from the
+ * projected modes (Parseval); the stopping tests are those of the per-kernel
+ * path.  on = 0 selects the per-kernel path (three kernels per CG iteration)
+ * for every problem.  Problems of other sizes or FP64 problems always use the
+ * per-kernel path, as does a device that cannot host a 16-CTA cluster of
+ * about 226 KB of shared memory per CTA.  Synchronises the device.  No
+ * counterpart in the paper. */
+int pff_set_cluster_mechanics(int on);
+
+/* Wait limit of every grid barrier of the persistent solve, in SM clock cycles
+ * (cycles > 0; 0 restores the default of 4e9 cycles, about two seconds at the
+ * maximum clock).  A block that is not released within the limit sets the
+ * problem's abort flag and returns; the other blocks return at their next
+ * barrier, the solve ends with PFF_ERR_BARRIER_TIMEOUT, the phase field is left
+ * unchanged and the handle stays usable.  A short limit (one cycle) makes the
+ * first barrier time out, which tests use to exercise that path.  Takes effect
+ * at the next launch.  Negative values: PFF_ERR_INVALID_ARG.  No counterpart in
+ * the paper. */
+int pff_set_barrier_spin_limit(long long cycles);
 
 /* Kernel timing for benchmarks.  When enabled, every launch of the library is
  * bracketed by CUDA events on its own stream; pff_timing_read returns the

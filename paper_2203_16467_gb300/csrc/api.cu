@@ -164,6 +164,7 @@ struct Twiddles {
 // k_persist.cu
 int persist_bccg_blocks(int share_den);
 cudaError_t launch_persist_bccg(const Desc<float>* d, int max_iters, int blocks, cudaStream_t st);
+void persist_set_spin(long long cycles);
 // micro.cu
 void micro_crack(double* out, int nx, int ny, double dx, double ell, double xc, double yc, double len, int shape,
                  int modulus, double E0, cudaStream_t st);
@@ -188,9 +189,17 @@ static int twiddles_for(int dev, Twiddles& out) {
     for (int i = 0; i < 2 * TWN; ++i) h32[i] = make_float2((float)h64[i].x, (float)h64[i].y);
     Twiddles t;
     if (cudaMalloc(&t.t32, sizeof(float2) * 2 * TWN) != cudaSuccess) return -1;
-    if (cudaMalloc(&t.t64, sizeof(double2) * 2 * TWN) != cudaSuccess) return -1;
-    cudaMemcpy(t.t32, h32.data(), sizeof(float2) * 2 * TWN, cudaMemcpyHostToDevice);
-    cudaMemcpy(t.t64, h64.data(), sizeof(double2) * 2 * TWN, cudaMemcpyHostToDevice);
+    if (cudaMalloc(&t.t64, sizeof(double2) * 2 * TWN) != cudaSuccess) { cudaFree(t.t32); return -1; }
+    // pageable sources: the device synchronisation makes the tables complete before kernels
+    // on any (non-blocking) stream can read them
+    if (cudaMemcpy(t.t32, h32.data(), sizeof(float2) * 2 * TWN, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t.t64, h64.data(), sizeof(double2) * 2 * TWN, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        cudaFree(t.t32);
+        cudaFree(t.t64);
+        cudaGetLastError();
+        return -1;
+    }
     tabs[dev] = t;
     out = t;
     return 0;
@@ -419,6 +428,29 @@ static const int CHUNK = 8;
 static bool g_graphs_enabled = true;
 static bool g_cond_nodes = false;  // BCCG explicit-residual chain in conditional graph nodes
 static bool g_persist = false;     // persistent BCCG solve for single FP32 512^2 problems (opt-in)
+static std::atomic<bool> g_cluster{true};   // cluster Newton-CG solve for FP32 512^2 problems (default on)
+
+// The mechanics solve of a group in one cluster launch (FP32 512 x 512 problems),
+// when enabled and the device can host it; returns false when the caller must
+// run the per-kernel path instead.
+template <typename T>
+static bool mech_cluster_group(const Group& g) {
+    if constexpr (sizeof(T) == 4) {
+        if (!g_cluster.load() || g.nx != 512 || g.ny != 512 || !mech_cluster_supported()) return false;
+        const bool tm = timing_on();   // kernel-class key: family 4 (cluster), op 0
+        if (tm) timing_begin(4 * 16 + 0, g.st);
+        cudaError_t e = launch_mech_cluster((const Desc<float>*)g.d_desc, g.np, g.st);
+        if (tm) timing_end(4 * 16 + 0, g.st);
+        if (e != cudaSuccess) {   // not launched: the per-kernel path runs instead
+            cudaGetLastError();
+            return false;
+        }
+        return true;
+    } else {
+        (void)g;
+        return false;
+    }
+}
 static int g_persist_share = 8;    // the persistent launch takes 1/share of the resident capacity
 
 template <typename T>
@@ -622,6 +654,7 @@ static int mech_solve_group(Group& g, int max_cg, int max_newton, pff_problem* e
     const int nx = g.nx, ny = g.ny, wp = g.wp, np = g.np;
     cudaStream_t st = g.st;
     int rc;
+    if (mech_cluster_group<T>(g)) return 0;
     for (int round = 0; round <= max_newton; ++round) {
         launch_row_fwd<T>(RF_NEWTON, nx, ny, d, np, st);
         launch_col<T>(CO_GAMMA_N, nx, ny, wp, d, np, st);
@@ -1306,6 +1339,7 @@ int pff_solve_mechanics(pff_problem* h, pff_step_report* out) {
         using T = decltype(tag);
         const Desc<T>* d = (const Desc<T>*)h->d_desc;
         launch_step_begin<T>(d, 1, h->st);
+        if (mech_cluster_group<T>(g)) return poll<T>(g, true, h);
         for (int round = 0; round <= p.mech_max_newton; ++round) {
             run_trio<T>(h, RF_NEWTON, CO_GAMMA_N, RI_NEWTON);
             for (int it = 0; it <= p.mech_max_cg + CHUNK; it += CHUNK) {
@@ -1663,6 +1697,19 @@ int pff_set_graphs(int on) {
 int pff_set_persistent(int on) {
     cudaDeviceSynchronize();
     g_persist = on != 0;
+    return PFF_OK;
+}
+
+int pff_set_cluster_mechanics(int on) {
+    cudaDeviceSynchronize();
+    g_cluster.store(on != 0);
+    return PFF_OK;
+}
+
+int pff_set_barrier_spin_limit(long long cycles) {
+    if (cycles < 0) return PFF_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    persist_set_spin(cycles);
     return PFF_OK;
 }
 

@@ -19,6 +19,8 @@
 // translation unit bypass L1 (-Xptxas -dlcm=cg at build), since L1 is not
 // coherent between the SMs within one kernel; spectrum rows are staged with
 // 16-byte-or-wider copies only where they are coherent (plain loads here).
+#include <atomic>
+
 #include "kernels.cuh"
 #include "launch.h"
 
@@ -27,7 +29,7 @@ namespace {
 
 constexpr int PB_NT = 128;                        // threads per block (the FP32 512-row pass geometry)
 constexpr int PB_CW = 2;                          // columns per column item (64 threads each)
-constexpr long long PB_SPIN_CYCLES = 4000000000LL;
+constexpr long long PB_SPIN_CYCLES = 4000000000LL;   // default wait limit of a barrier (about two seconds)
 
 using RC = RowCfg<float, 512, 1>;
 static_assert(RC::NT == PB_NT && RC::ROWS == 2, "row geometry of the persistent kernel");
@@ -35,10 +37,11 @@ static_assert(RC::NT == PB_NT && RC::ROWS == 2, "row geometry of the persistent 
 __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) { return *(const volatile unsigned*)p; }
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
 
-// Grid barrier with an optional reduction of NR double-float values (see above).
-// Returns false in every thread after a timeout or an abort.
+// Grid barrier with an optional reduction of NR values (double-float within the
+// block, FP64 across blocks).  A block waits at most `spin` clock cycles for the
+// release.  Returns false in every thread after a timeout or an abort.
 template <int NR, class FIN>
-__device__ bool grid_sync(Ctrl* c, double* part, DF (&v)[NR > 0 ? NR : 1], FIN fin) {
+__device__ bool grid_sync(Ctrl* c, double* part, DF (&v)[NR > 0 ? NR : 1], FIN fin, long long spin) {
     using O = RedOps<DF>;
     constexpr int NW = PB_NT / 32;
     constexpr int NRA = NR > 0 ? NR : 1;
@@ -62,7 +65,7 @@ __device__ bool grid_sync(Ctrl* c, double* part, DF (&v)[NR > 0 ? NR : 1], FIN f
             for (int k = 0; k < NR; ++k) {
                 DF x = sh[k][0];
                 for (int w = 1; w < NW; ++w) x = O::add(x, sh[k][w]);
-                O::store(part, (size_t)blockIdx.x * NR + k, x);
+                __stcg(part + (size_t)blockIdx.x * NR + k, O::total(x));   // FP64 block total
             }
         }
         __threadfence();
@@ -72,7 +75,7 @@ __device__ bool grid_sync(Ctrl* c, double* part, DF (&v)[NR > 0 ? NR : 1], FIN f
         if (!s_last) {
             const long long t0 = clock64();
             while (ld_volatile(&c->bar_gen) == gen) {
-                if (ld_volatile(&c->bar_abort) || clock64() - t0 > PB_SPIN_CYCLES) { s_ok = 0; break; }
+                if (ld_volatile(&c->bar_abort) || clock64() - t0 > spin) { s_ok = 0; break; }
                 __nanosleep(32);
             }
             __threadfence();
@@ -81,14 +84,16 @@ __device__ bool grid_sync(Ctrl* c, double* part, DF (&v)[NR > 0 ? NR : 1], FIN f
     __syncthreads();
     if (s_last) {
         double tot[NRA];
+        __shared__ double shd[NRA][NW];
         if constexpr (NR > 0) {
+            // FP64 cross-block sum in a fixed order
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
-                DF x = O::zero();
-                for (int b = threadIdx.x; b < (int)gridDim.x; b += PB_NT) x = O::add(x, O::load(part, (size_t)b * NR + k));
+                double x = 0.0;
+                for (int b = threadIdx.x; b < (int)gridDim.x; b += PB_NT) x += __ldcg(part + (size_t)b * NR + k);
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x = O::add(x, O::shfl(x, o));
-                if (lane == 0) sh[k][warp] = x;
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                if (lane == 0) shd[k][warp] = x;
             }
             __syncthreads();
         }
@@ -96,9 +101,9 @@ __device__ bool grid_sync(Ctrl* c, double* part, DF (&v)[NR > 0 ? NR : 1], FIN f
             if constexpr (NR > 0) {
 #pragma unroll
                 for (int k = 0; k < NR; ++k) {
-                    DF x = sh[k][0];
-                    for (int w = 1; w < NW; ++w) x = O::add(x, sh[k][w]);
-                    tot[k] = O::total(x);
+                    double x = shd[k][0];
+                    for (int w = 1; w < NW; ++w) x += shd[k][w];
+                    tot[k] = x;
                 }
             }
             fin(tot);
@@ -147,7 +152,7 @@ struct Fin {
 // Phases are compiled as separate (not inlined) functions so that the kernel's
 // register allocation is that of the largest phase, not of their union.
 template <class F>
-__device__ __noinline__ bool row_fwd_phase(const Desc<float>& d, float2* work, const float2* rtw) {
+__device__ __noinline__ bool row_fwd_phase(const Desc<float>& d, float2* work, const float2* rtw, long long spin) {
     const typename F::Ctx ctx = bcast_prep<F>(d);
     Acc<float> acc[1];
     for (int item = blockIdx.x; item < 512 / RC::ROWS; item += gridDim.x) {
@@ -157,22 +162,22 @@ __device__ __noinline__ bool row_fwd_phase(const Desc<float>& d, float2* work, c
         row_fwd_fft_store<float, 512, 1>(d, item * RC::ROWS, work, rtw);
     }
     DF none[1];
-    return grid_sync<0>(d.ctrl, d.part, none, NoFin{});
+    return grid_sync<0>(d.ctrl, d.part, none, NoFin{}, spin);
 }
 
 template <class OP>
-__device__ __noinline__ bool col_phase(const Desc<float>& d, float2* work, const float2* ctw) {
+__device__ __noinline__ bool col_phase(const Desc<float>& d, float2* work, const float2* ctw, long long spin) {
     const ModeK<float> mk(d);
     for (int item = blockIdx.x; item < d.wp / PB_CW; item += gridDim.x) {
         __syncthreads();
         col512_item<float, 1, OP, PB_CW>(d, mk, item * PB_CW, work, ctw);
     }
     DF none[1];
-    return grid_sync<0>(d.ctrl, d.part, none, NoFin{});
+    return grid_sync<0>(d.ctrl, d.part, none, NoFin{}, spin);
 }
 
 template <class F>
-__device__ __noinline__ bool row_inv_phase(const Desc<float>& d, float2* work, const float2* rtw) {
+__device__ __noinline__ bool row_inv_phase(const Desc<float>& d, float2* work, const float2* rtw, long long spin) {
     const typename F::Ctx ctx = bcast_prep<F>(d);
     Acc<float> acc[F::NR];
     for (int item = blockIdx.x; item < 512 / RC::ROWS; item += gridDim.x) {
@@ -182,24 +187,25 @@ __device__ __noinline__ bool row_inv_phase(const Desc<float>& d, float2* work, c
     DF v[F::NR];
 #pragma unroll
     for (int k = 0; k < F::NR; ++k) v[k] = acc[k].df();
-    return grid_sync<F::NR>(d.ctrl, d.part, v, Fin<F>{d});
+    return grid_sync<F::NR>(d.ctrl, d.part, v, Fin<F>{d}, spin);
 }
 
 template <class F>
-__device__ __noinline__ bool elem_phase(const Desc<float>& d) {
+__device__ __noinline__ bool elem_phase(const Desc<float>& d, long long spin) {
     const typename F::Ctx ctx = bcast_prep<F>(d);
     Acc<float> acc[F::NR];
     elem_items<float, F>(d, ctx, &acc[0]);
     DF v[F::NR];
 #pragma unroll
     for (int k = 0; k < F::NR; ++k) v[k] = acc[k].df();
-    return grid_sync<F::NR>(d.ctrl, d.part, v, Fin<F>{d});
+    return grid_sync<F::NR>(d.ctrl, d.part, v, Fin<F>{d}, spin);
 }
 
 constexpr int PB_WORK = RC::NSEQ * RC::SP > PB_CW * COL512_XS ? RC::NSEQ * RC::SP : PB_CW * COL512_XS;
 constexpr size_t PB_SMEM = (size_t)(RC::TWS + padded_len(512) + PB_WORK) * sizeof(float2);
 
-__global__ void __launch_bounds__(PB_NT, 4) k_bccg512(const Desc<float>* __restrict__ descs, int max_iters) {
+__global__ void __launch_bounds__(PB_NT, 4) k_bccg512(const Desc<float>* __restrict__ descs, int max_iters,
+                                                        long long spin) {
     const Desc<float>& d = descs[0];
     Ctrl* c = d.ctrl;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -212,14 +218,14 @@ __global__ void __launch_bounds__(PB_NT, 4) k_bccg512(const Desc<float>* __restr
     __syncthreads();
     for (int it = 0; it <= max_iters; ++it) {
         if (__ldcg(&c->pf_b) || ld_volatile(&c->bar_abort)) break;   // the same decision in every block
-        if (!row_fwd_phase<FPfA1<float>>(d, work, rtw)) return;
-        if (!col_phase<FColLapPF>(d, work, ctw)) return;
-        if (!row_inv_phase<FPfA3<float>>(d, work, rtw)) return;
-        if (!elem_phase<FPfB1<float>>(d)) return;
+        if (!row_fwd_phase<FPfA1<float>>(d, work, rtw, spin)) return;
+        if (!col_phase<FColLapPF>(d, work, ctw, spin)) return;
+        if (!row_inv_phase<FPfA3<float>>(d, work, rtw, spin)) return;
+        if (!elem_phase<FPfB1<float>>(d, spin)) return;
         if (__ldcg(&c->pf_full)) {
-            if (!row_fwd_phase<FPfVIn<float>>(d, work, rtw)) return;
-            if (!col_phase<FColLapPFFull>(d, work, ctw)) return;
-            if (!row_inv_phase<FPfB3<float>>(d, work, rtw)) return;
+            if (!row_fwd_phase<FPfVIn<float>>(d, work, rtw, spin)) return;
+            if (!col_phase<FColLapPFFull>(d, work, ctw, spin)) return;
+            if (!row_inv_phase<FPfB3<float>>(d, work, rtw, spin)) return;
         }
     }
 }
@@ -244,10 +250,16 @@ int persist_bccg_blocks(int share_den) {
     return b;
 }
 
+// Wait limit of the grid barriers in clock cycles (0: the default of about two seconds).
+static std::atomic<long long> g_spin{0};
+void persist_set_spin(long long cycles) { g_spin.store(cycles > 0 ? cycles : 0); }
+
 // Launches the persistent solve of one FP32 512 x 512 problem (after its BCCG start).
 cudaError_t launch_persist_bccg(const Desc<float>* d, int max_iters, int blocks, cudaStream_t st) {
     if (blocks < 1) return cudaErrorInvalidConfiguration;
-    void* args[] = {(void*)&d, (void*)&max_iters};
+    long long spin = g_spin.load();
+    if (spin <= 0) spin = PB_SPIN_CYCLES;
+    void* args[] = {(void*)&d, (void*)&max_iters, (void*)&spin};
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_bccg512, dim3(blocks), dim3(PB_NT), args, PB_SMEM, st);
     count_launch();
     return e;

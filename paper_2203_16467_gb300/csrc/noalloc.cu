@@ -80,8 +80,12 @@ int setup(int dev, DeviceSymbols& out, const char** msg) {
                 tw[M + j] = make_double2(std::cos(a), std::sin(a));
             }
         for (int j = 0; j < NA_TW; ++j) twf[j] = make_float2((float)tw[j].x, (float)tw[j].y);
+        // a copy from pageable memory may return before its DMA has landed, and kernels on
+        // non-blocking streams do not wait for the legacy stream: the device synchronisation
+        // makes the tables complete before any call can read them
         if (cudaMemcpyToSymbol(g_na_twiddles, tw, sizeof(double2) * NA_TW) != cudaSuccess ||
-            cudaMemcpyToSymbol(g_na_twiddles_f, twf, sizeof(float2) * NA_TW) != cudaSuccess) {
+            cudaMemcpyToSymbol(g_na_twiddles_f, twf, sizeof(float2) * NA_TW) != cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess) {
             *msg = "twiddle upload failed";
             cudaGetLastError();
             return PFF_ERR_CUDA;

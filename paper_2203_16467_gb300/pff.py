@@ -112,6 +112,8 @@ _SIGS = {
     "pff_set_graphs": (ctypes.c_int, [ctypes.c_int]),
     "pff_set_pdl": (ctypes.c_int, [ctypes.c_int]),
     "pff_set_persistent": (ctypes.c_int, [ctypes.c_int]),
+    "pff_set_barrier_spin_limit": (ctypes.c_int, [ctypes.c_longlong]),
+    "pff_set_cluster_mechanics": (ctypes.c_int, [ctypes.c_int]),
     "pff_apply_laplacian_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
                                                    ctypes.POINTER(ctypes.c_char_p)]),
     "pff_apply_laplacian_noalloc_f32": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
@@ -182,6 +184,16 @@ def kernel_launches():
 
 def set_persistent(on=True):
     return _check(lib.pff_set_persistent(1 if on else 0))
+
+
+def set_cluster_mechanics(on=True):
+    """Mechanics solves of FP32 512^2 problems in one cluster launch (True, default) or per kernel."""
+    return _check(lib.pff_set_cluster_mechanics(1 if on else 0))
+
+
+def set_barrier_spin_limit(cycles=0):
+    """Wait limit (clock cycles) of the persistent solve's grid barriers; 0: default."""
+    return _check(lib.pff_set_barrier_spin_limit(int(cycles)))
 
 
 def set_pdl(on=True):

@@ -4,6 +4,8 @@ state, and against the per-phase kernels over several load steps.  Its dot
 products are summed in a different (fixed) order than the per-phase kernels',
 so the comparison between the two GPU paths is within the mixed-precision
 tolerance, not bitwise."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -85,3 +87,45 @@ def test_persistent_load_steps_match_per_phase_kernels(pff, model):
         # the stopping tests fire depends on the summation order of the dot products
         assert abs(x["bccg_iters"] - y["bccg_iters"]) <= max(8, y["bccg_iters"] // 2), (x["bccg_iters"], y["bccg_iters"])
         np.testing.assert_allclose(x["eps_bar"], y["eps_bar"], rtol=1e-5, atol=1e-12)
+
+
+def test_persistent_barrier_timeout_returns_status_and_handle_stays_usable(pff):
+    # A one-cycle wait limit makes the first grid barrier of the persistent solve time out
+    # (the first block to arrive is never released within it): the kernel sets the abort
+    # flag, every block returns, and the call reports PFF_ERR_BARRIER_TIMEOUT with the
+    # phase field unchanged.  With the default limit the same handle then solves normally.
+    n, ell = 512, 4.0
+    E = modulus_field(n, n, 32.0, 5)
+    z = gaussian_field(n, n, 16.0, 6)
+    phi0 = 0.5 * (z - z.min()) / (z.max() - z.min())
+    em = eps_M(1.0, 0.2, 1.0, ell)
+    eb = (0.0, 1.3 * em, 0.0)
+    try:
+        pff.set_persistent(True)
+        p = pff.Problem(n, n, pff.MIXED, E=E, model=("AT1", "SPECTRAL", "CRACK_SET"),
+                        params=dict(nu=0.2, ell=ell, pf_tol=1e-8))
+        p.set_phase_field(phi0)
+        p.set_strain(None, eb)
+        pff.set_barrier_spin_limit(1)
+        rep = pff.StepReport()
+        rc = pff.lib.pff_solve_phase_field(p.h, ctypes.byref(rep))
+        assert rc == pff.ERR_BARRIER_TIMEOUT, rc
+        assert "timed out" in pff.lib.pff_last_error(p.h).decode()
+        np.testing.assert_array_equal(p.get_fields(pff.FIELD_PHI), phi0.astype(np.float32).astype(np.float64))
+        pff.set_barrier_spin_limit(0)
+        rep_ok = p.solve_phase_field()
+        phi_a = p.get_fields(pff.FIELD_PHI)
+        p.close()
+        pff.set_persistent(False)
+        q = pff.Problem(n, n, pff.MIXED, E=E, model=("AT1", "SPECTRAL", "CRACK_SET"),
+                        params=dict(nu=0.2, ell=ell, pf_tol=1e-8))
+        q.set_phase_field(phi0)
+        q.set_strain(None, eb)
+        q.solve_phase_field()
+        phi_b = q.get_fields(pff.FIELD_PHI)
+        q.close()
+    finally:
+        pff.set_barrier_spin_limit(0)
+        pff.set_persistent(False)
+    assert rep_ok["bccg_iters"] > 0
+    assert np.linalg.norm(phi_a - phi_b) / np.linalg.norm(phi_b) < 1e-5
