@@ -54,6 +54,9 @@ def build(force=False, verbose=False, jobs=None):
     for host_tu in ("api.cu", "noalloc.cu", "micro.cu"):
         jobs_list.append([cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, host_tu),
                           "-o", os.path.join(BUILD, host_tu.replace(".cu", ".o"))])
+    # the cluster mechanics solve (FP32 only)
+    jobs_list.append([cc, *ARCH, *FLAGS, "-DPFF_REAL=float", "-c", os.path.join(CSRC, "k_cluster.cu"),
+                      "-o", os.path.join(BUILD, "k_cluster.o")])
     # persistent kernels: their blocks read what other blocks of the same launch wrote,
     # so global loads bypass L1 (-dlcm=cg) and 8-byte staging copies use L2-only loads
     jobs_list.append([cc, *ARCH, *FLAGS, "-DPFF_REAL=float", "-DPFF_L2_ONLY", "-Xptxas", "-dlcm=cg", "-c",

@@ -267,7 +267,7 @@ bool smem_optin(const void* fn, size_t smem);
 bool timing_on();
 void timing_begin(int key, cudaStream_t st);
 void timing_end(int key, cudaStream_t st);
-enum { FAM_ROW_FWD = 0, FAM_ROW_INV = 1, FAM_COL = 2, FAM_ELEM = 3 };
+enum { FAM_ROW_FWD = 0, FAM_ROW_INV = 1, FAM_COL = 2, FAM_ELEM = 3, FAM_CLUSTER = 4 };
 
 template <typename T, int NX, int NC, class F>
 void go_row_fwd(const Desc<T>* d, int np, int ny, cudaStream_t st, int key) {

@@ -21,6 +21,9 @@ template <typename T> void launch_gather(const Desc<T>* d, int np, int* flags, v
 // sets the graph condition h to 1 when some problem of the group evaluates J v
 // explicitly in this BCCG iteration (its pf_full is set and it has not stopped)
 template <typename T> void launch_pf_cond(const Desc<T>* d, int np, cudaGraphConditionalHandle h, cudaStream_t st);
+// the whole mechanics solve of np FP32 512 x 512 problems, one thread-block cluster each (k_cluster.cu)
+bool mech_cluster_supported();
+cudaError_t launch_mech_cluster(const Desc<float>* d, int np, cudaStream_t st);
 void launch_convert_d2f(float* dst, const double* src, size_t n, cudaStream_t st);
 void launch_convert_f2d(double* dst, const float* src, size_t n, cudaStream_t st);
 
