@@ -389,7 +389,7 @@ int pff_set_pdl(int on);
 int pff_set_persistent(int on);
 
 /* Mechanics sub-problem of FP32 512 x 512 problems in one launch per solve
- * (default on): one thread-block cluster of 16 CTAs per problem keeps the
+ * (default off): one thread-block cluster of 16 CTAs per problem keeps the
  * three-component half spectrum in distributed shared memory, so the column
  * FFTs and the projection Gamma (Sec. 3.1.1) never move the spectrum through
  * HBM, and the Newton rounds and CG iterations (Eqs. mech_newton,
@@ -397,10 +397,14 @@ int pff_set_persistent(int on);
  * reductions.  The CG step lengths use p.Ap = p.(C_m:p) and r.Ap = r.(C_m:p),
  * exact for iterates in the range of the projection, and q.q from the
  * projected modes (Parseval); the stopping tests are those of the per-kernel
- * path.  on = 0 selects the per-kernel path (three kernels per CG iteration)
- * for every problem.  Problems of other sizes or FP64 problems always use the
+ * path.  Measured slower than the per-kernel path on GB300 (164 vs 53 us per
+ * CG iteration of one problem): the spectrum fills the shared memory of each
+ * SM, which then hosts one 8-warp CTA whose row steps are latency-bound, and
+ * the spectrum that the per-kernel path moves mostly stays in L2.  on = 0
+ * (default) selects the per-kernel path (three kernels per CG iteration) for
+ * every problem.  Problems of other sizes or FP64 problems always use the
  * per-kernel path, as does a device that cannot host a 16-CTA cluster of
- * about 226 KB of shared memory per CTA.  Synchronises the device.  No
+ * about 210 KB of shared memory per CTA.  Synchronises the device.  No
  * counterpart in the paper. */
 int pff_set_cluster_mechanics(int on);
 

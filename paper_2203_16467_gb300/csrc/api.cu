@@ -428,7 +428,7 @@ static const int CHUNK = 8;
 static bool g_graphs_enabled = true;
 static bool g_cond_nodes = false;  // BCCG explicit-residual chain in conditional graph nodes
 static bool g_persist = false;     // persistent BCCG solve for single FP32 512^2 problems (opt-in)
-static std::atomic<bool> g_cluster{true};   // cluster Newton-CG solve for FP32 512^2 problems (default on)
+static std::atomic<bool> g_cluster{false};  // cluster Newton-CG solve for FP32 512^2 problems (opt-in)
 
 // The mechanics solve of a group in one cluster launch (FP32 512 x 512 problems),
 // when enabled and the device can host it; returns false when the caller must

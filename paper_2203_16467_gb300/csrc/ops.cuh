@@ -1,11 +1,10 @@
 // ops.cuh -- per-pixel prologues / epilogues / finalizers of the load step.
 //
 // Mechanics (Sec. 3.1.1), one operator application per CG iteration:
-//   K1 row_fwd  FCgIn     : x += a p, r -= a q, p = r + b p (previous iteration's a, b);
-//                           r.r (FP64 sum); tau = C_m : p; FFT rows
+//   K1 row_fwd  FCgIn     : p = r + b p (previous iteration's b); tau = C_m : p; p.tau -> a;
+//                           FFT rows
 //   K2 col      FColGamma : Gamma projection between column FFTs
-//   K3 row_inv  FCgOut    : q = A p; p.q, r.q, q.q -> a = r.r/p.q,
-//                           r'.r' = r.r - 2a r.q + a^2 q.q, b = r'.r'/r.r
+//   K3 row_inv  FCgOut    : q = A p; x += a p, r -= a q; explicit r.r -> stop test, b
 // Newton residual (Eq. elasticity_nodal): FNewtonIn / FColGammaN / FNewtonOut.
 // Phase field (Algorithm 1), two operator applications per BCCG iteration:
 //   A1 FPfA1 (p = -r + b p, masked) -> A2 lap -> A3 FPfA3 (p.Jp, r.p -> alpha)
@@ -147,77 +146,82 @@ struct FNewtonOut {   // R = P sigma; CG start r = p = -R, theta = 0; Newton tes
     }
 };
 
+// CG iteration k, split over the operator's two row passes (Sec. 3.1.1; the CG of
+// Eq. elasticity_newton_linear):
+//   FCgIn  (row forward): p_k = r_k + beta_{k-1} p_{k-1} (k > 0), tau = C_m : p_k, the
+//          real FFT of tau along x; p_k.tau -> alpha_k = r_k.r_k / p_k.A p_k, where
+//          p.Ap = p.P tau = p.tau because every iterate lies in range(P) (P = F^-1 Gamma F,
+//          an orthogonal projection).
+//   FCgOut (row inverse): q = A p_k; theta += alpha p_k, r_{k+1} = r_k - alpha q; the
+//          explicit r_{k+1}.r_{k+1} -> stopping test and beta_k = r_{k+1}.r_{k+1} / r_k.r_k.
+// q is never stored.  Flags: FCgIn skips on cg_b (set by the previous FCgOut's stopping
+// test) and copies it to cg_a, which the column pass and FCgOut read.
 template <typename T>
 struct FCgIn {
     static constexpr int NR = 1;
-    struct Ctx { T alpha, beta; int upd; T eb[3]; int split; LameC<T> lm; };
-    __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->cg_a); }
+    struct Ctx { T beta; int upd; int iso; T eb[3]; int split; LameC<T> lm; };
+    __device__ static bool skip(const Desc<T>& d) {
+        int f = ldflag(&d.ctrl->cg_b);
+        if (blockIdx.x == 0 && threadIdx.x == 0) d.ctrl->cg_a = f;
+        return f;
+    }
     __device__ static Ctx prep(const Desc<T>& d) {
-        Ctx c{T(0), T(0), 0, {}, 0, LameC<T>(d)};
+        Ctx c{T(0), 0, 0, {}, 0, LameC<T>(d)};
         c.upd = ldflag(&d.ctrl->cg_it) > 0;
-        c.alpha = T(ldd(&d.ctrl->alpha));
         c.beta = T(ldd(&d.ctrl->beta));
         for (int k = 0; k < 3; ++k) c.eb[k] = T(ldd(&d.ctrl->eps_bar[k]));
         c.split = d.k.split;
+        c.iso = contact_of(d.k.split) == ISOTROPIC;   // the isotropic tangent does not depend on eps
         return c;
     }
     // two-phase pixel: all loads of a thread's pixels are issued before any store
-    struct In { T p[3], r[3], q[3], th[3], e[3], phi, E; };
+    struct In { T p[3], r[3], e[3], phi, E; };
     __device__ static In load(const Desc<T>& d, const Ctx& c, size_t i) {
         In a;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             a.p[k] = d.p[k][i];
-            a.r[k] = d.r[k][i];
-            a.e[k] = d.eps[k][i];
-            if (c.upd) { a.q[k] = d.q[k][i]; a.th[k] = d.th[k][i]; }
+            if (c.upd) a.r[k] = d.r[k][i];
+            a.e[k] = c.iso ? T(0) : d.eps[k][i];
         }
         a.phi = d.phi[i];
         a.E = d.E[i];
         return a;
     }
     __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, const In& a, T (&v)[3], Acc<T>* acc) {
-        T r[3], p[3];
+        T p[3];
         if (c.upd) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                T rk = a.r[k] - c.alpha * a.q[k];
-                d.th[k][i] = a.th[k] + c.alpha * a.p[k];
-                T pk = rk + c.beta * a.p[k];
-                d.r[k][i] = rk;
-                d.p[k][i] = pk;
-                r[k] = rk;
-                p[k] = pk;
+                p[k] = a.r[k] + c.beta * a.p[k];
+                d.p[k][i] = p[k];
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) { r[k] = a.r[k]; p[k] = a.p[k]; }
+            for (int k = 0; k < 3; ++k) p[k] = a.p[k];
         }
-        wdot(acc[0], r[0], r[1], r[2], r[0], r[1], r[2]);
         T lam = c.lm.lc * a.E, mu = c.lm.mc * a.E;
         tangent(c.split, c.eb[0] + a.e[0], c.eb[1] + a.e[1], c.eb[2] + a.e[2], hdeg(a.phi), lam, mu,
                 p[0], p[1], p[2], v);
+        wdot(acc[0], p[0], p[1], p[2], v[0], v[1], v[2]);
     }
     __device__ static void finalize(const Desc<T>& d, const double* tot) {
         Ctrl* c = d.ctrl;
-        double rr = tot[0];
-        c->rr = rr;
-        bool conv = sqrt(rr) <= c->cg_target;
-        if (conv || c->cg_it >= d.k.max_cg || c->cg_break) {
-            if (!conv && !c->cg_break) c->status |= 1;
+        const double pAp = tot[0];
+        c->pAp = pAp;
+        if (!(pAp > 0.0)) {   // p.Ap <= 0: stop (A8); every block has read cg_b already
+            c->cg_break = 1;
+            c->alpha = 0.0;
+            c->cg_a = 1;
             c->cg_b = 1;
         } else {
-            c->cg_b = 0;
+            c->alpha = c->rr / pAp;
         }
     }
 };
 
-struct FColGammaCG {   // CG column pass: copies cg_a = cg_b
-    template <typename T> __device__ static bool skip(const Desc<T>& d) {
-        int f = ldflag(&d.ctrl->cg_b);
-        if (blockIdx.x == 0 && threadIdx.x == 0) d.ctrl->cg_a = f;
-        return f;
-    }
+struct FColGammaCG {   // CG column pass (skips with cg_a)
+    template <typename T> __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->cg_a); }
     template <typename T> __device__ static void apply(const ModeK<T>& m, int kx, int ky, typename CT<T>::t (&v)[3]) {
         gamma_apply(m, kx, ky, v);
     }
@@ -225,41 +229,41 @@ struct FColGammaCG {   // CG column pass: copies cg_a = cg_b
 
 template <typename T>
 struct FCgOut {
-    static constexpr int NR = 3;
-    using Ctx = NoCtx;
-    __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->cg_b); }
-    __device__ static Ctx prep(const Desc<T>&) { return Ctx{}; }
-    struct In { T p[3], r[3]; };
+    static constexpr int NR = 1;
+    struct Ctx { T alpha; };
+    __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->cg_a); }
+    __device__ static Ctx prep(const Desc<T>& d) { return Ctx{T(ldd(&d.ctrl->alpha))}; }
+    struct In { T th[3], r[3], p[3]; };
     __device__ static In load(const Desc<T>& d, const Ctx&, size_t i) {
         In a;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) { a.p[k] = d.p[k][i]; a.r[k] = d.r[k][i]; }
+        for (int k = 0; k < 3; ++k) { a.th[k] = d.th[k][i]; a.r[k] = d.r[k][i]; a.p[k] = d.p[k][i]; }
         return a;
     }
-    __device__ static void pixel(const Desc<T>& d, const Ctx&, size_t i, const In& a, T (&v)[3], Acc<T>* acc) {
-        d.q[0][i] = v[0]; d.q[1][i] = v[1]; d.q[2][i] = v[2];
-        wdot(acc[0], a.p[0], a.p[1], a.p[2], v[0], v[1], v[2]);
-        wdot(acc[1], a.r[0], a.r[1], a.r[2], v[0], v[1], v[2]);
-        wdot(acc[2], v[0], v[1], v[2], v[0], v[1], v[2]);
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, const In& a, T (&v)[3], Acc<T>* acc) {
+        T r[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            d.th[k][i] = a.th[k] + c.alpha * a.p[k];
+            r[k] = a.r[k] - c.alpha * v[k];
+            d.r[k][i] = r[k];
+        }
+        wdot(acc[0], r[0], r[1], r[2], r[0], r[1], r[2]);
     }
     __device__ static void finalize(const Desc<T>& d, const double* tot) {
         Ctrl* c = d.ctrl;
-        double pAp = tot[0];
-        c->pAp = pAp; c->rAp = tot[1]; c->qq = tot[2];
-        if (!(pAp > 0.0)) {
-            c->cg_break = 1;
-            c->alpha = 0.0;
-            c->beta = 0.0;
-        } else {
-            double rr = c->rr;
-            double a = rr / pAp;
-            double rn = rr - 2.0 * a * tot[1] + a * a * tot[2];
-            if (rn < 0.0) rn = 0.0;
-            c->alpha = a;
-            c->beta = rr > 0.0 ? rn / rr : 0.0;
-        }
+        const double rr = tot[0], rr_old = c->rr;
         c->cg_it += 1;
         c->cg_total += 1;
+        c->beta = rr_old > 0.0 ? rr / rr_old : 0.0;
+        c->rr = rr;
+        const bool conv = sqrt(rr) <= c->cg_target;
+        if (conv || c->cg_it >= d.k.max_cg) {
+            if (!conv) c->status |= 1;
+            c->cg_b = 1;
+        } else {
+            c->cg_b = 0;
+        }
     }
 };
 

@@ -187,7 +187,7 @@ def set_persistent(on=True):
 
 
 def set_cluster_mechanics(on=True):
-    """Mechanics solves of FP32 512^2 problems in one cluster launch (True, default) or per kernel."""
+    """Mechanics solves of FP32 512^2 problems in one cluster launch (True) or per kernel (False, default)."""
     return _check(lib.pff_set_cluster_mechanics(1 if on else 0))
 
 

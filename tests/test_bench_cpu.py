@@ -10,11 +10,14 @@ import bench
 def test_bytes_per_iteration_512():
     b = bench.bytes_per_px(4, 512)
     s = 8 * 257 / 512                                   # half-spectrum bytes per pixel per component
-    assert b[(0, 1)] == pytest.approx(26 * 4 + 3 * s)  # 116.05: the dominant kernel
+    assert b[(0, 1)] == pytest.approx(14 * 4 + 3 * s)  # 68.05: read p, r, eps*, phi, E; write p, S
+    assert b[(1, 1)] == pytest.approx(15 * 4 + 3 * s)  # 72.05: read S, theta, r, p; write theta, r
     cg = b[(0, 1)] + b[(2, 1)] + b[(1, 1)]
     bccg = b[(0, 3)] + b[(2, 4)] + b[(1, 4)] + b[(3, 11)]
     explicit = b[(0, 4)] + b[(2, 6)] + b[(1, 5)]
-    assert round(cg) == 188 and round(bccg) == 82 and round(explicit) == 46
+    assert round(cg) == 164 and round(bccg) == 82 and round(explicit) == 46
+    bi = bench.bytes_per_px(4, 512, iso=True)          # the isotropic tangent reads no strain
+    assert round(bi[(0, 1)] + bi[(2, 1)] + bi[(1, 1)]) == 152
     b8 = bench.bytes_per_px(8, 512)
     for k in b:
         # FP64 doubles each value but the one-byte flag plane
@@ -27,7 +30,7 @@ def test_active_launches_follow_the_reports():
             [{"mech_cg_iters": 4, "newton_iters": 1, "bccg_iters": 5, "bccg_full_iters": 1},
              {"mech_cg_iters": 0, "newton_iters": 0, "bccg_iters": 0, "bccg_full_iters": 0}]]
     a = bench.active_launches(reps)
-    assert a[(0, 1)] == 17 and a[(2, 1)] == 14 and a[(1, 1)] == 14
+    assert a[(0, 1)] == 14 and a[(2, 1)] == 14 and a[(1, 1)] == 14
     assert all(a[k] == 12 for k in ((0, 3), (2, 4), (1, 4), (3, 11)))
     assert all(a[k] == 4 for k in ((0, 4), (2, 6), (1, 5)))
     assert set(a) == set(bench.KERNEL_NAMES)

@@ -20,7 +20,7 @@ def pff():
     __graft_entry__.build()
     from paper_2203_16467_gb300 import pff as m
     yield m
-    m.set_cluster_mechanics(True)
+    m.set_cluster_mechanics(False)
 
 
 def _state(seed=3, amp=0.9):
@@ -95,7 +95,7 @@ def test_cluster_load_steps_match_per_kernel_path(pff):
         pff.destroy_batch(b)
         for p in probs:
             p.close()
-    pff.set_cluster_mechanics(True)
+    pff.set_cluster_mechanics(False)
     (ra, pa, ea), (rb, pb, eb_) = out[True], out[False]
     for j in range(len(variants)):
         assert [r["incremented"] for r in ra[j]] == [r["incremented"] for r in rb[j]]

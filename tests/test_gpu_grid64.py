@@ -83,26 +83,29 @@ def _iou(a, b):
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
 def test_whole_run_crack_set(pff, gold, prec):
+    # The oracle's own runs of this workload at tolerances 1e-7, 1e-8 and 1e-10 end with two
+    # crack sets (phi > 0.95) that differ in exactly three pixels (two crack tails): which
+    # tail a run takes is decided at the level of the sub-solvers' stopping iterations
+    # (tests/golden/make_grid64_run.py --tolerance-family).  What is unique is the crack set
+    # outside those pixels, which every run must reproduce exactly; on the three pixels the
+    # run must take one of the oracle's two tails as a whole.
     par = params()
     E = modulus_field(N, N, LC, SEED)
     p = _problem(pff, prec, par, E)
     reps = p.step_load(5000)
     assert reps[-1]["broken"]
     phi = p.get_fields(pff.FIELD_PHI)
-    ious = {"tol1e-08": float(_iou(phi > 0.95, gold["phi_final"] > 0.95))}
-    fam = np.load(FAMILY)
-    ious.update({k.replace("phi_final_", ""): float(_iou(phi > 0.95, fam[k] > 0.95))
-                 for k in fam.files if k.startswith("phi_final")})
-    print("whole-run IoU", prec, ious, "steps", len(reps), "oracle steps", int(gold["n_steps"]))
-    if prec == 0:
-        # FP64 with the oracle's stopping rules: the crack set of the oracle's run at the
-        # workload's own tolerance (1e-8)
-        assert ious["tol1e-08"] >= 0.98, (ious, len(reps), int(gold["n_steps"]))
-    else:
-        # FP32 rounding perturbs every solve at about the level that separates the oracle's
-        # own runs at neighbouring tolerances, whose crack tails differ by three pixels
-        # (tests/golden/make_grid64_run.py --tolerance-family): the mixed run is compared
-        # with that family
-        assert max(ious.values()) >= 0.98, (ious, len(reps), int(gold["n_steps"]))
-    assert phi.min() >= -1e-12 and phi.max() <= 1.0 + 1e-6
     p.close()
+    fam = np.load(FAMILY)
+    tails = [gold["phi_final"] > 0.95] + [fam[k] > 0.95 for k in fam.files if k.startswith("phi_final")]
+    amb = np.zeros_like(tails[0])
+    for t in tails[1:]:
+        amb |= t ^ tails[0]
+    assert 0 < amb.sum() <= 3
+    crack = phi > 0.95
+    ious = [float(_iou(crack, t)) for t in tails]
+    print("whole-run IoU", prec, ious, "steps", len(reps), "oracle steps", int(gold["n_steps"]))
+    assert np.array_equal(crack & ~amb, tails[0] & ~amb), int(np.sum((crack ^ tails[0]) & ~amb))
+    assert any(np.array_equal(crack[amb], t[amb]) for t in tails), (crack[amb], [t[amb] for t in tails])
+    assert max(ious) == 1.0
+    assert phi.min() >= -1e-12 and phi.max() <= 1.0 + 1e-6
