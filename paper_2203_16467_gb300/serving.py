@@ -1,18 +1,24 @@
 """Continuous-batching server for whole crack-path simulations.
 
 Requests (a grid size, a model variant, a microstructure seed) arrive over
-time.  Each tick the server admits queued requests while batch slots and the
-HBM budget allow (pff_batch_admit fails with OOM otherwise and the request
-waits), advances every admitted simulation by one load step with one
-pff_batch_step call (simulations of equal size and precision share every
-kernel launch; different sizes run concurrently on their own streams), and
-retires simulations that broke (C-bar < C_broken) or reached their step cap,
-freeing their slot and memory.  All simulation state (E, phi, eps*, solver
-vectors) stays resident on the device between ticks.
+time.  Simulations of one grid size form a lane: one batch (pff_create_batch),
+one CUDA stream and one worker thread, which advances all of the lane's
+simulations by one load step per pff_batch_step call (simulations of equal size
+and precision share every kernel launch) and, between two of its own steps,
+admits the simulations handed to it and retires those that broke
+(C-bar < C_broken) or reached their step cap.  Lanes run independently, so a
+request never waits for a load step of another grid size: a 128^2 request that
+arrives during a 1024^2 step starts within one 128^2 step.  The request loop
+admits arrived requests while the HBM budget (the sum of pff_problem_bytes of
+the admitted simulations) and the slot count allow; a request that does not
+fit waits for a retirement.  All simulation state (E, phi, eps*, solver
+vectors) stays resident on the device between load steps.
 
-Latencies: per load step (the tick that advanced a simulation) and per
-simulation (arrival to retirement), reported as p50 / p99.
+Latencies: per load step (the step that advanced a simulation), start
+(arrival to the start of the simulation's first step) and per simulation
+(arrival to retirement), reported as p50 / p99, overall and per grid size.
 """
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -43,121 +49,253 @@ class Request:
 class Sim:
     req: Request
     problem: object
-    slot: int
-    admitted: float
+    bytes: int
+    stream: object = None         # keeps the problem's own stream alive
+    slot: int = -1
     steps: int = 0
+    started: float = None
     reports: list = field(default_factory=list)
+
+
+def _new_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.Stream()
+    except ImportError:
+        pass
+    return None
+
+
+def _pct(a, q):
+    return float(np.percentile(a, q)) if len(a) else None
+
+
+class Lane:
+    """The simulations of one grid size: a batch on its own stream, stepped by a worker thread."""
+
+    def __init__(self, server, key):
+        self.server = server
+        self.key = key
+        self.cuda_stream = _new_stream()
+        sp = self.cuda_stream.cuda_stream if self.cuda_stream is not None else None
+        self.batch = pff.create_batch(server.max_slots, 1 << 62, sp)   # the server keeps the HBM budget
+        self.pending = []
+        self.sims = {}
+        self.steps_log = []           # (t_start, t_end) of every batch step of the lane
+        self.cv = threading.Condition()
+        self.stop = False
+        self.error = None
+        self.thread = threading.Thread(target=self._work, daemon=True)
+        self.thread.start()
+
+    def hand(self, sim):
+        with self.cv:
+            self.pending.append(sim)
+            self.cv.notify()
+
+    def busy(self):
+        with self.cv:
+            return bool(self.pending or self.sims)
+
+    def _work(self):
+        srv = self.server
+        try:
+            while True:
+                with self.cv:
+                    while not (self.pending or self.sims or self.stop):
+                        self.cv.wait()
+                    if self.stop:
+                        return
+                    new, self.pending = self.pending, []
+                for sim in new:   # between two steps of this lane
+                    sim.slot = pff.batch_admit(self.batch, sim.problem.h)
+                    self.sims[sim.slot] = sim
+                t0 = srv.now()
+                out = pff.batch_step(self.batch, srv.max_slots, 1)
+                t1 = srv.now()
+                self.steps_log.append((t0, t1))
+                finished = []
+                for slot, sim in self.sims.items():
+                    reps = out[slot]
+                    if not reps:
+                        continue
+                    if sim.started is None:
+                        sim.started = t0
+                    sim.steps += 1
+                    sim.reports.append(reps[0])
+                    srv.record_step(self.key, t1 - t0)
+                    if reps[0]["broken"] or sim.steps >= sim.req.max_steps:
+                        finished.append(slot)
+                for slot in finished:
+                    sim = self.sims.pop(slot)
+                    pff.batch_release(self.batch, slot)
+                    srv.retire(sim, self.key)
+        except Exception as e:   # reported by the request loop
+            self.error = e
+            with self.cv:
+                for sim in self.pending:
+                    srv.release_budget(sim)
+                self.pending = []
+            srv.wake()
+
+    def close(self):
+        """Stop after the current step; simulations still running are retired as they are."""
+        with self.cv:
+            self.stop = True
+            self.cv.notify()
+        self.thread.join()
+        for slot, sim in list(self.sims.items()):
+            pff.batch_release(self.batch, slot)
+            self.server.retire(sim, self.key)
+        self.sims = {}
+        for sim in self.pending:
+            sim.problem.close()
+            self.server.release_budget(sim)
+        self.pending = []
+        pff.destroy_batch(self.batch)
 
 
 class Server:
     def __init__(self, hbm_budget, max_slots=64, stream=None, keep_fields=False):
+        self.budget = int(hbm_budget)
         self.max_slots = max_slots
-        self.batch = pff.create_batch(max_slots, int(hbm_budget), stream)
-        self.stream = stream
-        self.queue = []
-        self.active = {}
-        self.done = {}
-        self.step_latencies = []
-        self.sim_latencies = []
-        self.load_steps = 0
+        self.stream = stream          # kept for compatibility: lanes and problems use their own streams
         self.keep_fields = keep_fields
+        self.queue = []
+        self.lanes = {}
+        self.done = {}
+        self.used = 0
+        self.active = 0
+        self.peak_active = 0
+        self.load_steps = 0
+        self.step_lat = {}
+        self.start_lat = {}
+        self.sim_lat = {}
+        self.mu = threading.Lock()
+        self.wake_cv = threading.Condition(self.mu)
         self.t0 = None
 
+    # ---- time base and bookkeeping (called from the lanes' threads too)
+    def now(self):
+        return time.perf_counter() - self.t0
+
+    def wake(self):
+        with self.wake_cv:
+            self.wake_cv.notify_all()
+
+    def record_step(self, key, dt):
+        with self.mu:
+            self.step_lat.setdefault(key, []).append(dt)
+            self.load_steps += 1
+
+    def release_budget(self, sim):
+        with self.mu:
+            self.used -= sim.bytes
+            self.active -= 1
+
+    def retire(self, sim, key):
+        res = {"steps": sim.steps, "broken": bool(sim.reports[-1]["broken"]) if sim.reports else False,
+               "reports": sim.reports, "latency": self.now() - sim.req.arrival,
+               "start_latency": (sim.started - sim.req.arrival) if sim.started is not None else None, "n": key}
+        if self.keep_fields:
+            res["phi"] = sim.problem.get_fields(pff.FIELD_PHI)
+        sim.problem.close()
+        with self.wake_cv:
+            self.used -= sim.bytes
+            self.active -= 1
+            self.sim_lat.setdefault(key, []).append(res["latency"])
+            if res["start_latency"] is not None:
+                self.start_lat.setdefault(key, []).append(res["start_latency"])
+            self.done[sim.req.rid] = res
+            self.wake_cv.notify_all()
+
+    # ---- requests
     def submit(self, req):
-        self.queue.append(req)
+        """Queue a request (thread-safe; it is admitted once its arrival time has passed)."""
+        with self.wake_cv:
+            self.queue.append(req)
+            self.wake_cv.notify_all()
 
     def _make(self, r):
         em = eps_M(1.0, 0.2, 1.0, r.ell)
         E = modulus_field(r.n, r.n, r.lc, r.seed)
-        p = pff.Problem(r.n, r.n, r.precision, stream=self.stream, E=E,
+        st = _new_stream()
+        p = pff.Problem(r.n, r.n, r.precision, stream=st.cuda_stream if st is not None else None, E=E,
                         model=(r.fracture, r.split, r.irreversibility),
                         params=dict(nu=0.2, ell=r.ell, mech_tol=r.tol, pf_tol=r.tol,
                                     d_eps_bar=(0.0, em / 20, 0.0)))
         if r.preload:
             p.set_strain(None, (0.0, r.preload * em, 0.0))
-        return p
-
-    def _now(self):
-        return time.perf_counter() - self.t0
+        return p, st
 
     def _admit(self):
-        now = self._now()
+        """Hand every arrived request that fits the budget and the slots to its lane."""
+        now = self.now()
         waiting = []
-        for r in self.queue:
-            if r.arrival > now or len(self.active) >= self.max_slots:
+        with self.mu:
+            queued, self.queue = self.queue, []
+        for r in sorted(queued, key=lambda q: q.arrival):
+            nb = pff.problem_bytes(r.n, r.n, r.precision)
+            with self.mu:
+                fits = r.arrival <= now and self.active < self.max_slots and self.used + nb <= self.budget
+                if fits:
+                    self.used += nb
+                    self.active += 1
+                    self.peak_active = max(self.peak_active, self.active)
+            if not fits:
                 waiting.append(r)
                 continue
-            p = self._make(r)
-            slot = pff.batch_admit(self.batch, p.h)
-            if slot is None:          # does not fit the HBM budget now
-                p.close()
-                waiting.append(r)
-                continue
-            self.active[slot] = Sim(r, p, slot, now)
-        self.queue = waiting
+            p, st = self._make(r)
+            key = (r.n, r.precision)
+            if key not in self.lanes:
+                self.lanes[key] = Lane(self, key)
+            self.lanes[key].hand(Sim(r, p, nb, st))
+        with self.mu:
+            self.queue = waiting + self.queue   # (requests submitted meanwhile stay queued)
 
-    def tick(self):
-        """Admit, advance every active simulation by one load step, retire finished ones.
-        Returns the number of simulations advanced."""
+    def run(self, poll_s=0.0005):
+        """Serve until every submitted request is done; returns stats()."""
         if self.t0 is None:
             self.t0 = time.perf_counter()
-        self._admit()
-        if not self.active:
-            return 0
-        t = time.perf_counter()
-        out = pff.batch_step(self.batch, self.max_slots, 1)
-        dt = time.perf_counter() - t
-        n = 0
-        for slot, sim in list(self.active.items()):
-            reps = out[slot]
-            if not reps:
-                continue
-            n += 1
-            sim.steps += 1
-            sim.reports.append(reps[0])
-            self.step_latencies.append(dt)
-            if reps[0]["broken"] or sim.steps >= sim.req.max_steps:
-                self._retire(slot)
-        self.load_steps += n
-        return n
-
-    def _retire(self, slot):
-        sim = self.active.pop(slot)
-        pff.batch_release(self.batch, slot)
-        res = {"steps": sim.steps, "broken": bool(sim.reports[-1]["broken"]), "reports": sim.reports,
-               "latency": self._now() - sim.req.arrival}
-        if self.keep_fields:
-            res["phi"] = sim.problem.get_fields(pff.FIELD_PHI)
-        self.sim_latencies.append(res["latency"])
-        sim.problem.close()
-        self.done[sim.req.rid] = res
-
-    def run(self, max_ticks=10 ** 9):
-        if self.t0 is None:
-            self.t0 = time.perf_counter()
-        ticks = 0
-        while (self.queue or self.active) and ticks < max_ticks:
-            if not self.active and self.queue:
-                wait = min(r.arrival for r in self.queue) - self._now()
-                if wait > 0:
-                    time.sleep(wait)
-            self.tick()
-            ticks += 1
+        while True:
+            for lane in self.lanes.values():
+                if lane.error is not None:
+                    raise lane.error
+            self._admit()
+            with self.mu:
+                queued = bool(self.queue)
+            if not queued and not any(lane.busy() for lane in self.lanes.values()):
+                break
+            with self.wake_cv:
+                nxt = min((r.arrival for r in self.queue), default=None)
+                wait = poll_s if nxt is None else max(0.0, min(poll_s, nxt - self.now()))
+                self.wake_cv.wait(timeout=max(wait, 1e-4))
         return self.stats()
 
     def stats(self):
-        el = self._now() if self.t0 is not None else 0.0
-        pct = (lambda a, q: float(np.percentile(a, q)) if len(a) else None)
+        el = self.now() if self.t0 is not None else 0.0
+        allv = (lambda d: [x for v in d.values() for x in v])
+        per = {}
+        for key in sorted(set(self.step_lat) | set(self.sim_lat)):
+            n = key[0]
+            per[f"{n}x{n}" + ("" if key[1] == pff.MIXED else "_fp64")] = {
+                "requests": len(self.sim_lat.get(key, [])),
+                "step_latency_s": {"p50": _pct(self.step_lat.get(key, []), 50), "p99": _pct(self.step_lat.get(key, []), 99)},
+                "start_latency_s": {"p50": _pct(self.start_lat.get(key, []), 50),
+                                    "p99": _pct(self.start_lat.get(key, []), 99)},
+                "sim_latency_s": {"p50": _pct(self.sim_lat.get(key, []), 50), "p99": _pct(self.sim_lat.get(key, []), 99)}}
         return {"load_steps": self.load_steps, "seconds": el,
                 "load_steps_per_s": self.load_steps / el if el > 0 else None,
-                "step_latency_s": {"p50": pct(self.step_latencies, 50), "p99": pct(self.step_latencies, 99)},
-                "sim_latency_s": {"p50": pct(self.sim_latencies, 50), "p99": pct(self.sim_latencies, 99)},
-                "completed": len(self.done)}
+                "step_latency_s": {"p50": _pct(allv(self.step_lat), 50), "p99": _pct(allv(self.step_lat), 99)},
+                "start_latency_s": {"p50": _pct(allv(self.start_lat), 50), "p99": _pct(allv(self.start_lat), 99)},
+                "sim_latency_s": {"p50": _pct(allv(self.sim_lat), 50), "p99": _pct(allv(self.sim_lat), 99)},
+                "per_size": per, "completed": len(self.done), "peak_active": self.peak_active}
 
     def close(self):
-        for slot in list(self.active):
-            self._retire(slot)
-        pff.destroy_batch(self.batch)
+        for lane in self.lanes.values():
+            lane.close()
+        self.lanes = {}
 
 
 def poisson_requests(n_requests, rate_per_s, sizes=(128, 256, 512, 1024), seed=0, max_steps=200, **kw):

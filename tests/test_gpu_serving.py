@@ -1,5 +1,9 @@
-"""Continuous batching: admission by HBM budget, and each simulation's result is the
-same alone and in a mix of other sizes and model variants that arrive while it runs."""
+"""Continuous batching: admission by HBM budget, each simulation's result is the same alone
+and in a mix of other sizes and model variants that arrive while it runs, and a request never
+waits for a load step of another grid size."""
+import threading
+import time
+
 import numpy as np
 import pytest
 
@@ -24,23 +28,23 @@ def _req(serving, pff, rid, n, fracture, split, irr, seed, arrival=0.0, prec=Non
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
 def test_result_same_alone_and_in_mix(srv, prec):
     pff, serving, torch = srv
-    stream = torch.cuda.Stream()
     budget = 4 << 30
     a = lambda arr: _req(serving, pff, 0, 64, "AT1", "SPECTRAL", "CRACK_SET", 7, arrival=arr, prec=prec)
-    alone = serving.Server(budget, max_slots=8, stream=stream.cuda_stream, keep_fields=True)
+    alone = serving.Server(budget, max_slots=8, keep_fields=True)
     alone.submit(a(0.0))
     alone.run()
     ref = alone.done[0]
     alone.close()
-    mix = serving.Server(budget, max_slots=8, stream=stream.cuda_stream, keep_fields=True)
+    mix = serving.Server(budget, max_slots=8, keep_fields=True)
     mix.submit(_req(serving, pff, 1, 128, "AT2", "ISOTROPIC", "DAMAGE", 3, prec=prec))
     mix.submit(_req(serving, pff, 2, 64, "AT1", "ISOTROPIC", "DAMAGE", 4, prec=prec))
     mix.submit(_req(serving, pff, 3, 256, "AT2", "SPECTRAL", "CRACK_SET", 5, prec=prec, steps=10))
     mix.submit(a(0.0))
-    mix.tick()                              # 0 is admitted with the others ...
-    mix.submit(_req(serving, pff, 4, 64, "AT2", "SPECTRAL", "DAMAGE", 6, prec=prec))   # ... 4 arrives later
+    # arrives while the others run: joins the 64x64 lane between two of its steps
+    mix.submit(_req(serving, pff, 4, 64, "AT2", "SPECTRAL", "DAMAGE", 6, arrival=0.02, prec=prec))
     mix.run()
     got = mix.done[0]
+    assert mix.done[4]["steps"] > 0
     mix.close()
     assert got["steps"] == ref["steps"]
     tol = 1e-12 if prec == 0 else 1e-6
@@ -56,12 +60,34 @@ def test_admission_respects_hbm_budget(srv):
     server = serving.Server(int(2.5 * one), max_slots=8)
     for i in range(5):
         server.submit(_req(serving, pff, i, 128, "AT1", "SPECTRAL", "CRACK_SET", i, steps=3))
-    peak = 0
-    while server.queue or server.active:
-        server.tick()
-        peak = max(peak, len(server.active))
-    st = server.stats()
+    st = server.run()
     server.close()
-    assert peak == 2
+    assert st["peak_active"] == 2
     assert st["completed"] == 5
     assert st["step_latency_s"]["p99"] >= st["step_latency_s"]["p50"] > 0
+
+
+def test_small_request_does_not_wait_for_a_large_step(srv):
+    # a 64x64 request that arrives while a 1024x1024 simulation is inside a load step starts,
+    # and finishes its first step, before that 1024x1024 step ends
+    pff, serving, torch = srv
+    server = serving.Server(8 << 30, max_slots=8)
+    server.submit(_req(serving, pff, 0, 1024, "AT1", "SPECTRAL", "CRACK_SET", 1, steps=6))
+    th = threading.Thread(target=server.run)
+    th.start()
+    key = (1024, pff.MIXED)
+    t_end = time.time() + 120
+    while time.time() < t_end and not (key in server.lanes and server.lanes[key].steps_log):
+        time.sleep(0.001)
+    arrival = server.now()
+    server.submit(_req(serving, pff, 1, 64, "AT1", "SPECTRAL", "CRACK_SET", 2, arrival=arrival, steps=1))
+    th.join()
+    log = server.lanes[key].steps_log
+    small = server.done[1]
+    server.close()
+    assert small["steps"] == 1 and server.done[0]["steps"] == 6
+    # the large step running at (or, in a gap between steps, right after) the arrival
+    end = next(e for s, e in log if e > arrival)
+    first_start = arrival + small["start_latency"]
+    assert first_start < end, (arrival, first_start, end, log)
+    assert small["latency"] < end - arrival
