@@ -292,6 +292,36 @@ int pff_apply_laplacian(pff_problem* h, const double* in, double* out);
 int pff_constitutive(pff_problem* h, const double* eps3, const double* phi, const double* p3,
                      double* sig3, double* psi, double* tang3);
 
+/* Kernel variants (no counterpart in the paper); both variants of a kind compute
+ * the same method, only the summation order of their reductions differs
+ * (results agree to the rounding of the storage precision, not bitwise).
+ *   PFF_VARIANT_COLUMN_SHAPE: the 512-point FP32 column pass with ncomp (1 or 3)
+ *     components (grid_n = 512): variant 0 = four spectrum columns per
+ *     256-thread block (default), 1 = two columns per 128-thread block (twice the
+ *     blocks: more SMs busy when a launch carries one simulation).
+ *   PFF_VARIANT_BCCG_PASSES (grid_n, ncomp ignored): variant 0 = Algorithm 1 in
+ *     three operator passes per iteration (the step length alpha from the column
+ *     pass by Parseval, the iterate fused into the J p pass; default), 1 = four
+ *     passes (alpha from p.Jp summed in real space, the iterate in its own
+ *     elementwise kernel; what the preconditioned option always uses).
+ * Takes effect at the next launch; captured CUDA graphs are re-captured.
+ * Synchronises the device.  Unsupported arguments: PFF_ERR_INVALID_ARG. */
+enum { PFF_VARIANT_COLUMN_SHAPE = 2, PFF_VARIANT_BCCG_PASSES = 3 };
+int pff_set_kernel_variant(int kind, int grid_n, int ncomp, int variant);
+int pff_get_kernel_variant(int kind, int grid_n, int ncomp, int* variant);
+
+/* Autotuner of the kernel variants on ordinary load steps of a batch: each of
+ * the eight combinations (one-component column shape, three-component column
+ * shape, BCCG passes) = (c & 1, (c >> 1) & 1, (c >> 2) & 1), c = 0..7, runs
+ * steps_each + 1 load steps in the batch's own launch configuration (the first
+ * after a change is not timed: graphs are re-captured), scored by
+ * pixel-iterations per second of host wall time; the best combination stays
+ * set and is returned in chosen[3]; scores[8] (optional) receives the eight
+ * scores.  reports / steps_done as pff_batch_autotune (per slot,
+ * 8 (steps_each + 1) entries).  The steps advance the batch's simulations. */
+int pff_batch_autotune_kernels(pff_batch* b, int steps_each, int* chosen, double* scores, pff_step_report* reports,
+                               int* steps_done);
+
 /* Batching: several problems (any sizes, precisions, models) advanced
  * together.  pff_batch_admit fails with PFF_ERR_OOM if the problem's device
  * bytes do not fit the remaining budget or PFF_ERR_STATE if all slots are

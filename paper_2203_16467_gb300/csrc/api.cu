@@ -92,8 +92,19 @@ static void timing_collect() {
 }
 
 void note_launch_error(cudaError_t e);
+// FFT shape variants: columns per block of the 512-point FP32 column pass, for one (index 0) and
+// three (index 1) components; a change bumps the generation, and graph caches captured with
+// another generation are re-captured
+static std::atomic<int> g_col512_cw[2] = {{4}, {4}};
+static std::atomic<int> g_shape_gen{0};
+// BCCG iteration structure: three passes (alpha from the column pass, iterate fused into the
+// J p pass; default) or the four-pass chain of the preconditioned variant (alpha from p.Jp)
+static std::atomic<bool> g_bccg4{false};
+int col512_cw(int nc);
 // Opt a kernel in to its dynamic shared memory when static plus dynamic shared
 // memory exceeds the 48 KB available without the attribute.
+int col512_cw(int nc) { return g_col512_cw[nc == 3 ? 1 : 0].load(std::memory_order_relaxed); }
+
 bool smem_optin(const void* fn, size_t smem) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -233,6 +244,7 @@ struct GraphCache {
     int np = 0;
     int cond = -1;                     // conditional-node setting the graphs were captured with
     int precond = -1;                  // preconditioner setting the graphs were captured with
+    int gen = -1;                      // FFT shape generation the graphs were captured with
     void reset() {
         for (int k = 0; k < 2; ++k) {
             if (exec[k]) cudaGraphExecDestroy(exec[k]);
@@ -469,10 +481,16 @@ static void chunk_direct(int kind, const Group& g) {
                 launch_col<T>(CO_PRECOND, nx, ny, wp, d, np, st);
                 launch_row_inv<T>(RI_PF_Z, nx, ny, d, np, st);
             }
-            launch_row_fwd<T>(RF_PF_A, nx, ny, d, np, st);
-            launch_col<T>(CO_LAP_PF, nx, ny, wp, d, np, st);
-            launch_row_inv<T>(RI_PF_A, nx, ny, d, np, st);
-            launch_elem<T>(EL_PF_B, nx, ny, d, np, st);
+            if (g.precond || g_bccg4.load()) {
+                launch_row_fwd<T>(RF_PF_A, nx, ny, d, np, st);
+                launch_col<T>(CO_LAP_PF, nx, ny, wp, d, np, st);
+                launch_row_inv<T>(RI_PF_A, nx, ny, d, np, st);
+                launch_elem<T>(EL_PF_B, nx, ny, d, np, st);
+            } else {   // alpha from the column pass, the iterate fused into the J p pass
+                launch_row_fwd<T>(RF_PF_A, nx, ny, d, np, st);
+                launch_col<T>(CO_LAP_PFQ, nx, ny, wp, d, np, st);
+                launch_row_inv<T>(RI_PF_AB, nx, ny, d, np, st);
+            }
             launch_row_fwd<T>(RF_PF_B, nx, ny, d, np, st);          // only when J v is evaluated
             launch_col<T>(CO_LAP_PF_FULL, nx, ny, wp, d, np, st);   // explicitly this iteration
             launch_row_inv<T>(RI_PF_B, nx, ny, d, np, st);
@@ -520,12 +538,20 @@ static cudaError_t capture_pf_chunk(const Group& g, cudaGraph_t* out, int* kerne
             launch_row_inv<T>(RI_PF_Z, nx, ny, d, np, st);
             nk += 3;
         }
-        launch_row_fwd<T>(RF_PF_A, nx, ny, d, np, st);
-        launch_col<T>(CO_LAP_PF, nx, ny, wp, d, np, st);
-        launch_row_inv<T>(RI_PF_A, nx, ny, d, np, st);
-        launch_elem<T>(EL_PF_B, nx, ny, d, np, st);
+        if (g.precond || g_bccg4.load()) {
+            launch_row_fwd<T>(RF_PF_A, nx, ny, d, np, st);
+            launch_col<T>(CO_LAP_PF, nx, ny, wp, d, np, st);
+            launch_row_inv<T>(RI_PF_A, nx, ny, d, np, st);
+            launch_elem<T>(EL_PF_B, nx, ny, d, np, st);
+            nk += 4;
+        } else {
+            launch_row_fwd<T>(RF_PF_A, nx, ny, d, np, st);
+            launch_col<T>(CO_LAP_PFQ, nx, ny, wp, d, np, st);
+            launch_row_inv<T>(RI_PF_AB, nx, ny, d, np, st);
+            nk += 3;
+        }
         launch_pf_cond<T>(d, np, h, st);
-        nk += 5;
+        nk += 1;
         cudaStreamCaptureStatus cs;
         const cudaGraphNode_t* deps = nullptr;
         size_t nd = 0;
@@ -578,12 +604,14 @@ static void run_chunk(int kind, Group& g, bool& warmed) {
         warmed = true;   // attributes (shared-memory opt-in) are set by the first direct chunk
         return;
     }
-    if (gc->desc != g.d_desc || gc->np != g.np || gc->cond != (int)g_cond_nodes || gc->precond != g.precond) {
+    if (gc->desc != g.d_desc || gc->np != g.np || gc->cond != (int)g_cond_nodes || gc->precond != g.precond ||
+        gc->gen != g_shape_gen.load()) {
         gc->reset();
         gc->desc = g.d_desc;
         gc->np = g.np;
         gc->cond = (int)g_cond_nodes;
         gc->precond = g.precond;
+        gc->gen = g_shape_gen.load();
     }
     if (gc->failed[kind]) {
         chunk_direct<T>(kind, g);
@@ -1389,9 +1417,13 @@ int pff_solve_phase_field(pff_problem* h, pff_step_report* out) {
         }
         for (int it = 0; it <= p.pf_max_iter + CHUNK; it += CHUNK) {
             for (int c = 0; c < CHUNK; ++c) {
-                if (p.pf_precondition) run_trio<T>(h, RF_PF_Z, CO_PRECOND, RI_PF_Z);
-                run_trio<T>(h, RF_PF_A, CO_LAP_PF, RI_PF_A);
-                launch_elem<T>(EL_PF_B, h->nx, h->ny, d, 1, h->st);
+                if (p.pf_precondition || g_bccg4.load()) {
+                    if (p.pf_precondition) run_trio<T>(h, RF_PF_Z, CO_PRECOND, RI_PF_Z);
+                    run_trio<T>(h, RF_PF_A, CO_LAP_PF, RI_PF_A);
+                    launch_elem<T>(EL_PF_B, h->nx, h->ny, d, 1, h->st);
+                } else {
+                    run_trio<T>(h, RF_PF_A, CO_LAP_PFQ, RI_PF_AB);
+                }
                 run_trio<T>(h, RF_PF_B, CO_LAP_PF_FULL, RI_PF_B);
             }
             int r2 = poll<T>(g, false, h);
@@ -1596,6 +1628,89 @@ int pff_batch_autotune(pff_batch* b, const int* group_sizes, int n_candidates, i
     int rc = pff_batch_set_group_size(b, best);
     if (rc) return rc;
     if (chosen) *chosen = best;
+    return status;
+}
+
+int pff_set_kernel_variant(int kind, int grid_n, int ncomp, int variant) {
+    if (variant < 0 || variant > 1) return PFF_ERR_INVALID_ARG;
+    if (kind == PFF_VARIANT_COLUMN_SHAPE) {
+        if (grid_n != 512 || (ncomp != 1 && ncomp != 3)) return PFF_ERR_INVALID_ARG;
+        cudaDeviceSynchronize();
+        g_col512_cw[ncomp == 3 ? 1 : 0].store(variant == 1 ? 2 : 4);
+    } else if (kind == PFF_VARIANT_BCCG_PASSES) {
+        cudaDeviceSynchronize();
+        g_bccg4.store(variant == 1);
+    } else {
+        return PFF_ERR_INVALID_ARG;
+    }
+    g_shape_gen.fetch_add(1);
+    return PFF_OK;
+}
+
+int pff_get_kernel_variant(int kind, int grid_n, int ncomp, int* variant) {
+    if (!variant) return PFF_ERR_INVALID_ARG;
+    if (kind == PFF_VARIANT_COLUMN_SHAPE) {
+        if (grid_n != 512 || (ncomp != 1 && ncomp != 3)) return PFF_ERR_INVALID_ARG;
+        *variant = g_col512_cw[ncomp == 3 ? 1 : 0].load() == 2 ? 1 : 0;
+        return PFF_OK;
+    }
+    if (kind == PFF_VARIANT_BCCG_PASSES) {
+        *variant = g_bccg4.load() ? 1 : 0;
+        return PFF_OK;
+    }
+    return PFF_ERR_INVALID_ARG;
+}
+
+int pff_batch_autotune_kernels(pff_batch* b, int steps_each, int* chosen, double* scores, pff_step_report* reports,
+                               int* steps_done) {
+    if (!b || steps_each < 1) return PFF_ERR_INVALID_ARG;
+    // candidates: (one-component column shape, three-component column shape, BCCG structure)
+    constexpr int NCAND = 8;
+    int cand[NCAND][3];
+    for (int c = 0; c < NCAND; ++c) { cand[c][0] = c & 1; cand[c][1] = (c >> 1) & 1; cand[c][2] = (c >> 2) & 1; }
+    auto apply = [&](int c) {
+        int rc = pff_set_kernel_variant(PFF_VARIANT_COLUMN_SHAPE, 512, 1, cand[c][0]);
+        if (!rc) rc = pff_set_kernel_variant(PFF_VARIANT_COLUMN_SHAPE, 512, 3, cand[c][1]);
+        if (!rc) rc = pff_set_kernel_variant(PFF_VARIANT_BCCG_PASSES, 0, 1, cand[c][2]);
+        return rc;
+    };
+    const int per = steps_each + 1;   // one untimed step after each change (graph re-capture)
+    const int total = NCAND * per;
+    std::vector<int> done(b->max_slots, 0);
+    int status = PFF_OK, best = 0;
+    double best_score = -1.0;
+    for (int c = 0; c < NCAND; ++c) {
+        int rc = apply(c);
+        if (rc) return rc;
+        double elapsed = 0.0, work = 0.0;
+        for (int s = 0; s < per; ++s) {
+            std::vector<pff_step_report> one(b->max_slots);
+            std::vector<int> d1(b->max_slots, 0);
+            const auto t0 = std::chrono::steady_clock::now();
+            rc = pff_batch_step(b, 1, one.data(), d1.data());
+            const auto t1 = std::chrono::steady_clock::now();
+            if (rc && rc != PFF_ERR_NOT_CONVERGED) return rc;
+            if (rc) status = rc;
+            for (int i = 0; i < b->max_slots; ++i) {
+                if (!d1[i]) continue;
+                const pff_step_report& r = one[i];
+                if (reports) reports[(size_t)i * total + done[i]] = r;
+                ++done[i];
+                if (s > 0 && b->slot[i])
+                    work += (double)(r.mech_cg_iters + r.newton_iters + r.bccg_iters) * b->slot[i]->nx * b->slot[i]->ny;
+            }
+            if (s > 0) elapsed += std::chrono::duration<double>(t1 - t0).count();
+        }
+        const double score = elapsed > 0.0 ? work / elapsed : 0.0;
+        if (scores) scores[c] = score;
+        if (score > best_score) { best_score = score; best = c; }
+    }
+    if (steps_done)
+        for (int i = 0; i < b->max_slots; ++i) steps_done[i] = done[i];
+    int rc = apply(best);
+    if (rc) return rc;
+    if (chosen)
+        for (int k = 0; k < 3; ++k) chosen[k] = cand[best][k];
     return status;
 }
 

@@ -50,6 +50,7 @@ struct Ctrl {
     int istar, flag, rescaled;
     // phase field (Algorithm 1)
     double pf_rr, pf_rp, pJp, pf_alpha, pf_beta, pf_target, pf_best;
+    double pf_pap;          // sum a p^2 of the direction (the diagonal part of p.Jp)
     int pf_a, pf_b, pf_it, pf_break, n_active, pf_best_it, pf_clamp_iters;
     // residual recurrence: pf_full = this iteration evaluates Jv explicitly
     int pf_full, pf_force, pf_confirm, pf_since_full, pf_full_iters;

@@ -469,6 +469,11 @@ template <class OP> struct HasModePrep<OP, decltype((void)&OP::template mode_pre
     static constexpr bool value = true;
 };
 
+// Column multipliers may also reduce over the modes they see (before multiplying):
+// OP::NR values, OP::accum(mk, kx, ky, v, acc) per mode, OP::finalize(d, tot) once.
+template <class OP, class = void> struct ColNR { static constexpr int value = 0; };
+template <class OP> struct ColNR<OP, decltype((void)OP::NR, void())> { static constexpr int value = OP::NR; };
+
 // skip test and mode constants of a column pass, evaluated once per block
 template <typename T, class OP>
 struct ColPrep {
@@ -507,11 +512,14 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
     cp_async_wait_all();
     __syncthreads();
     fft_smem<T, NY, Cfg::NSEQ, SP, NT, false, Cfg::TW_SMEM>(buf, tw);
+    constexpr int NRA = ColNR<OP>::value > 0 ? ColNR<OP>::value : 1;
+    Acc<T> acc[NRA];
     for (int t = threadIdx.x; t < CW * NY; t += NT) {
         const int ky = t % NY, j = t / NY;
         C v[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) v[c] = buf[(c * CW + j) * SP + pidx(ky)];
+        if constexpr (ColNR<OP>::value > 0) OP::accum(mk, kx0 + j, ky, v, acc);
         OP::apply(mk, kx0 + j, ky, v);
 #pragma unroll
         for (int c = 0; c < NC; ++c) buf[(c * CW + j) * SP + pidx(ky)] = v[c];
@@ -522,6 +530,11 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
     for (int t = threadIdx.x; t < TOT; t += NT) {
         const int j = t % CW, ky = (t / CW) % NY, c = t / (CW * NY);
         d.S[c * plane + (unsigned)ky * d.wp + kx0 + j] = buf[(c * CW + j) * SP + pidx(ky)];
+    }
+    if constexpr (ColNR<OP>::value > 0) {
+        double tot[ColNR<OP>::value];
+        if (reduce_acc<ColNR<OP>::value, NT>(acc, d.part, &d.ctrl->counter, gridDim.x, tot) && threadIdx.x == 0)
+            OP::finalize(d, tot);
     }
 }
 
@@ -540,7 +553,7 @@ __global__ void __launch_bounds__(ColCfg<T, NY, NC>::NT) k_col(const Desc<T>* __
 // mod 16 complex slots): stage-1 value (k1, n0) at 72 k1 + n0 + n0/8, stage-2
 // value (k1, a, c) at 72 k1 + 9 a + c; every access of a warp touches each
 // bank pair at most twice (FP32).
-constexpr int COL512_CW = 4;       // columns per block (one 32-byte sector per row in FP32)
+constexpr int COL512_CW = 4;       // default columns per block (one 32-byte sector per row in FP32; 2 selectable)
 constexpr int COL512_XS = 584;     // exchange slots per component and column
 
 template <typename C, bool INV>
@@ -616,7 +629,7 @@ __device__ __forceinline__ void stage_col512_twiddles(const Desc<T>& d, typename
 // Column pass of the CW columns kx0.. of the half spectrum (64 CW threads).
 template <typename T, int NC, class OP, int CW>
 __device__ __forceinline__ void col512_item(const Desc<T>& d, const ModeK<T>& mk, int kx0, typename CT<T>::t* xb,
-                                            const typename CT<T>::t* tws) {
+                                            const typename CT<T>::t* tws, Acc<T>* acc = nullptr) {
     using C = typename CT<T>::t;
     const int j = threadIdx.x % CW, t = threadIdx.x / CW;
     const int kx = kx0 + j;
@@ -635,6 +648,7 @@ __device__ __forceinline__ void col512_item(const Desc<T>& d, const ModeK<T>& mk
         C v[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) v[c] = u[c][e];
+        if constexpr (ColNR<OP>::value > 0) OP::accum(mk, kx, k1 + 8 * cc + 64 * e, v, acc);
         OP::apply(mk, kx, k1 + 8 * cc + 64 * e, v);
 #pragma unroll
         for (int c = 0; c < NC; ++c) u[c][e] = v[c];
@@ -647,8 +661,8 @@ __device__ __forceinline__ void col512_item(const Desc<T>& d, const ModeK<T>& mk
         for (int e = 0; e < 8; ++e) d.S[c * plane + (unsigned)(tp + 64 * e) * d.wp + kx] = u[c][e];
 }
 
-template <typename T, int NC, class OP>
-__global__ void __launch_bounds__(64 * COL512_CW) k_col512(const Desc<T>* __restrict__ descs) {
+template <typename T, int NC, class OP, int CW = COL512_CW>
+__global__ void __launch_bounds__(64 * CW) k_col512(const Desc<T>* __restrict__ descs) {
     using C = typename CT<T>::t;
     const Desc<T>& d = descs[blockIdx.y];
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -658,7 +672,15 @@ __global__ void __launch_bounds__(64 * COL512_CW) k_col512(const Desc<T>* __rest
     ModeK<T> mk;
     if (block_prep<ColPrep<T, OP>>(d, mk)) return;
     stage_col512_twiddles<T>(d, tws);   // waited for inside the item, after its loads are issued
-    col512_item<T, NC, OP, COL512_CW>(d, mk, blockIdx.x * COL512_CW, xb, tws);
+    constexpr int NRA = ColNR<OP>::value > 0 ? ColNR<OP>::value : 1;
+    Acc<T> acc[NRA];
+    col512_item<T, NC, OP, CW>(d, mk, blockIdx.x * CW, xb, tws, acc);
+    if constexpr (ColNR<OP>::value > 0) {
+        double tot[ColNR<OP>::value];
+        if (reduce_acc<ColNR<OP>::value, 64 * CW>(acc, d.part, &d.ctrl->counter, gridDim.x, tot) &&
+            threadIdx.x == 0)
+            OP::finalize(d, tot);
+    }
 }
 
 // ---------------------------------------------------------------------------

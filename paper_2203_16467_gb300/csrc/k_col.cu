@@ -15,6 +15,7 @@ void launch_col(int op, int nx, int ny, int wp, const Desc<T>* d, int np, cudaSt
         case CO_LAP_PLAIN: PFF_SIZE_SWITCH(ny, (go_col<T, N_, 1, FColLapPlain>(d, np, wp, st, FAM_COL * 16 + op))); break;
         case CO_LAP_PF_FULL: PFF_SIZE_SWITCH(ny, (go_col<T, N_, 1, FColLapPFFull>(d, np, wp, st, FAM_COL * 16 + op))); break;
         case CO_PRECOND: PFF_SIZE_SWITCH(ny, (go_col<T, N_, 1, FColPrecond>(d, np, wp, st, FAM_COL * 16 + op))); break;
+        case CO_LAP_PFQ: PFF_SIZE_SWITCH(ny, (go_col<T, N_, 1, FColLapPFQ>(d, np, wp, st, FAM_COL * 16 + op))); break;
         case CO_LOWPASS: PFF_SIZE_SWITCH(ny, (go_col<T, N_, 1, FColLowPass>(d, np, wp, st, FAM_COL * 16 + op))); break;
         default: break;
     }

@@ -13,6 +13,7 @@ void launch_row_inv(int op, int nx, int ny, const Desc<T>* d, int np, cudaStream
         case RI_PF_A: PFF_SIZE_SWITCH(nx, (go_row_inv<T, N_, 1, FPfA3<T>>(d, np, ny, st, FAM_ROW_INV * 16 + op))); break;
         case RI_PF_B: PFF_SIZE_SWITCH(nx, (go_row_inv<T, N_, 1, FPfB3<T>>(d, np, ny, st, FAM_ROW_INV * 16 + op))); break;
         case RI_PF_Z: PFF_SIZE_SWITCH(nx, (go_row_inv<T, N_, 1, FPfZOut<T>>(d, np, ny, st, FAM_ROW_INV * 16 + op))); break;
+        case RI_PF_AB: PFF_SIZE_SWITCH(nx, (go_row_inv<T, N_, 1, FPfA3B<T>>(d, np, ny, st, FAM_ROW_INV * 16 + op))); break;
         case RI_COPY3: PFF_SIZE_SWITCH(nx, (go_row_inv<T, N_, 3, FCopyOut<T, 3>>(d, np, ny, st, FAM_ROW_INV * 16 + op))); break;
         case RI_COPY1: PFF_SIZE_SWITCH(nx, (go_row_inv<T, N_, 1, FCopyOut<T, 1>>(d, np, ny, st, FAM_ROW_INV * 16 + op))); break;
         default: break;

@@ -263,6 +263,8 @@ inline void launch_pdl(void (*fn)(P...), dim3 grid, dim3 block, size_t smem, cud
     if (e != cudaSuccess) note_launch_error(e);
 }
 bool smem_optin(const void* fn, size_t smem);
+// columns per block of the 512-point FP32 column pass with nc components (4 or 2; see pff_set_fft_variant)
+int col512_cw(int nc);
 // optional per-kernel-class event timing (see pff_timing_enable); key = family * 16 + op
 bool timing_on();
 void timing_begin(int key, cudaStream_t st);
@@ -296,10 +298,17 @@ void go_col(const Desc<T>* d, int np, int wp, cudaStream_t st, int key) {
     const bool tm = timing_on();
     if (tm) timing_begin(key, st);
     if constexpr (NY == 512 && sizeof(T) == 4) {   // register-resident radix-8 stages (FP64: too many registers)
-        using Cfg = Col512Cfg<T, NC>;
-        auto fn = k_col512<T, NC, OP>;
-        smem_optin((const void*)fn, Cfg::SMEM);
-        launch_pdl<T>(fn, dim3(wp / COL512_CW, np), dim3(Cfg::NT), Cfg::SMEM, st, d);
+        if (col512_cw(NC) == 2) {   // shape variant: 2 columns (128 threads) per block
+            using Cfg = Col512Cfg<T, NC, 2>;
+            auto fn = k_col512<T, NC, OP, 2>;
+            smem_optin((const void*)fn, Cfg::SMEM);
+            launch_pdl<T>(fn, dim3(wp / 2, np), dim3(Cfg::NT), Cfg::SMEM, st, d);
+        } else {
+            using Cfg = Col512Cfg<T, NC, COL512_CW>;
+            auto fn = k_col512<T, NC, OP, COL512_CW>;
+            smem_optin((const void*)fn, Cfg::SMEM);
+            launch_pdl<T>(fn, dim3(wp / COL512_CW, np), dim3(Cfg::NT), Cfg::SMEM, st, d);
+        }
     } else {
         using Cfg = ColCfg<T, NY, NC>;
         auto fn = k_col<T, NY, NC, OP>;

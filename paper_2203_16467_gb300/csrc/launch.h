@@ -7,8 +7,9 @@ namespace pff {
 template <typename T> struct Desc;
 
 enum RowFwdOp { RF_NEWTON, RF_CG, RF_PHI, RF_PF_A, RF_PF_B, RF_COPY3, RF_COPY1, RF_PF_Z };
-enum RowInvOp { RI_NEWTON, RI_CG, RI_LAP, RI_ENERGY, RI_PF_A, RI_PF_B, RI_COPY3, RI_COPY1, RI_PF_Z };
-enum ColOp { CO_GAMMA_N, CO_GAMMA_CG, CO_GAMMA_PLAIN, CO_LAP_DF, CO_LAP_PF, CO_LAP_PLAIN, CO_LAP_PF_FULL, CO_LOWPASS, CO_PRECOND };
+enum RowInvOp { RI_NEWTON, RI_CG, RI_LAP, RI_ENERGY, RI_PF_A, RI_PF_B, RI_COPY3, RI_COPY1, RI_PF_Z, RI_PF_AB };
+enum ColOp { CO_GAMMA_N, CO_GAMMA_CG, CO_GAMMA_PLAIN, CO_LAP_DF, CO_LAP_PF, CO_LAP_PLAIN, CO_LAP_PF_FULL, CO_LOWPASS, CO_PRECOND,
+             CO_LAP_PFQ };
 enum ElemOp { EL_FOLD, EL_PF_INIT, EL_POST, EL_DF, EL_CONSTITUTIVE, EL_STATE, EL_DRIVING, EL_FLAGS,
               EL_SAVE_CON, EL_SAVE_PHI, EL_RESTORE_PHI, EL_PF_B };
 

@@ -392,7 +392,7 @@ struct FCopyOut {
 // v_con = phi_con(phi_n) - phi_n <= 0; v^0 = 0; r^0 = -b masked; p^0 = -r^0.
 template <typename T>
 struct FPfInit {
-    static constexpr int NR = 3;
+    static constexpr int NR = 4;
     struct Ctx { double g; int resc; double eb[3]; double eta_dt; int frozen; };
     __device__ static bool skip(const Desc<T>&) { return false; }
     __device__ static Ctx prep(const Desc<T>& d) {
@@ -438,6 +438,7 @@ struct FPfInit {
         acc[0].addp(r, r);
         acc[1].addp(b, b);
         acc[2].add(a);
+        acc[3].addp(a * r, r);   // sum a p^2 of the first direction p = -r
     }
     __device__ static void finalize(const Desc<T>& d, const double* tot) {
         Ctrl* c = d.ctrl;
@@ -457,6 +458,8 @@ struct FPfInit {
         c->pf_rsel = 0;
         c->pf_abar = tot[2] * k.inv_n;
         c->pf_rz = 0.0;
+        c->pf_pap = tot[3];
+        c->pf_rp = -tot[0];
         c->bar_count = 0;
         c->bar_abort = 0;
         c->pf_last_full = rn;
@@ -611,6 +614,55 @@ struct FPfA3 {   // J p; p.Jp, r.p -> alpha = -(r.p)/(p.Jp)
     }
 };
 
+// ---- Algorithm 1 iteration in three operator passes (the default, unpreconditioned path)
+// p.Jp = sum a p^2 - kappa sum p lap_N p, and -sum p lap_N p = (1/(nx ny)) sum_k |2 pi q|^2
+// |p^_k|^2 over the full spectrum (Parseval), so alpha = -(r.p)/(p.Jp) is known after the
+// column pass, and the row-inverse pass that forms J p applies the iterate at once:
+//   FPfA1      (row forward): p = -r + beta p, zero on the active set
+//   FColLapPFQ (column)     : sum over the modes of w(kx) |2 pi q|^2 |p^|^2 (w = 2 on the kx
+//                             columns that stand for two modes, else 1); alpha
+//   FPfA3B     (row inverse): J p = a p - kappa lap_N p; v = max(v + alpha p, v_con); the
+//                             residual recurrence R + alpha J p; active set; r' and its dots
+// sum a p^2 and r.p of the next direction p' = -r' + beta p (free pixels; 0 on the active set)
+// come from sums of the iteration that forms r': sum a p'^2 = S1 - 2 beta S2 + beta^2 S3 and
+// r'.p' = -r'.r' + beta S4 with S1 = sum a r'^2, S2 = sum a r' p, S3 = sum a p^2 (free
+// pixels) and S4 = r'.p (pf_next_dir); the first direction p = -r from the start's sums.
+// (The preconditioned variant and the persistent kernel keep FPfA1 / FColLapPF / FPfA3 / FPfB1.)
+struct FColLapPFQ {
+    static constexpr int NR = 1;
+    template <typename T> __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
+    template <typename T>
+    __device__ static void accum(const ModeK<T>& m, int kx, int ky, const typename CT<T>::t (&v)[1], Acc<T>* acc) {
+        if (2 * kx > m.nx) return;   // padding columns of the spectrum rows hold no modes
+        const T qx = T(kx) * m.cx, qy = T(signed_k(ky, m.ny)) * m.cy;
+        const T w = (kx == 0 || 2 * kx == m.nx) ? T(1) : T(2);
+        const T q2 = w * (qx * qx + qy * qy);
+        acc[0].addp(q2 * v[0].x, v[0].x);
+        acc[0].addp(q2 * v[0].y, v[0].y);
+    }
+    template <typename T> __device__ static void apply(const ModeK<T>& m, int kx, int ky, typename CT<T>::t (&v)[1]) {
+        lap_apply(m, kx, ky, v);
+    }
+    template <typename T> __device__ static void finalize(const Desc<T>& d, const double* tot) {
+        Ctrl* c = d.ctrl;
+        const double pJp = c->pf_pap + d.k.kappa * tot[0] * d.k.inv_n;
+        c->pJp = pJp;
+        if (!(pJp > 0.0)) {
+            c->pf_break = 1;
+            c->pf_alpha = 0.0;
+        } else {
+            c->pf_alpha = -c->pf_rp / pJp;
+        }
+    }
+};
+
+// sum a p'^2 and r'.p' of the next direction p' = -r' + beta p from S1..S4 (see above)
+__device__ __forceinline__ void pf_next_dir(Ctrl* c, const double* S) {
+    const double b = c->pf_beta;
+    c->pf_pap = S[0] - 2.0 * b * S[1] + b * b * S[2];
+    c->pf_rp = -c->pf_rr + b * S[3];
+}
+
 // Iteration end shared by the fused iterate kernel (recurrence residual) and the
 // explicit residual kernel: beta, ||r||, active count and the stopping decision.
 template <typename T>
@@ -717,6 +769,59 @@ struct FPfB1 {
 };
 
 template <typename T>
+struct FPfA3B {   // J p from the column pass's lap p, then the iterate of FPfB1
+    static constexpr int NR = 8;
+    struct Ctx { T kappa; T alpha; double alpha_d; const T* ro; T* rn; };
+    __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a); }
+    __device__ static Ctx prep(const Desc<T>& d) {
+        const int sel = ldflag(&d.ctrl->pf_rsel);
+        const double a = ldd(&d.ctrl->pf_alpha);
+        return Ctx{T(d.k.kappa), T(a), a, pf_r(d, sel), pf_r(d, sel ^ 1)};
+    }
+    struct In { T p, a, v, vc, R, ro; };
+    __device__ static In load(const Desc<T>& d, const Ctx& c, size_t i) {
+        return In{d.th[2][i], d.r[0][i], d.th[0][i], d.r[2][i], d.lap[i], c.ro[i]};
+    }
+    __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, const In& a, T (&lp)[1], Acc<T>* acc) {
+        const T Jp = a.a * a.p - c.kappa * lp[0];
+        T x = a.v + c.alpha * a.p;
+        if (x < a.vc) { x = a.vc; acc[0].add(T(1)); }
+        d.th[0][i] = x;
+        const bool at = (x == a.vc);
+        T rn = a.R + c.alpha * Jp;
+        d.lap[i] = rn;
+        bool pos = false;
+        if (at) {   // the sign only matters at the bound (FP64 where FP32 is not decisive, as FPfB1)
+            if constexpr (sizeof(T) == 8) {
+                pos = rn > T(0);
+            } else {
+                T mag = fabs(a.R) + fabs(c.alpha * Jp);
+                if (fabs(rn) > T(4e-7) * mag) pos = rn > T(0);
+                else pos = recur_positive_fp64(a.R, c.alpha_d, Jp);
+            }
+        }
+        const bool active = at && pos;
+        if (active) rn = T(0);
+        c.rn[i] = rn;
+        d.flags[i] = (uint8_t)((at ? 1 : 0) | (active ? 2 : 0));
+        acc[1].addp(rn, rn);
+        acc[2].addp(rn, a.ro);
+        acc[3].add(active ? T(1) : T(0));
+        if (!active) {   // sums of the next direction (free pixels)
+            const T ar = a.a * rn;
+            acc[4].addp(ar, rn);
+            acc[5].addp(ar, a.p);
+            acc[6].addp(a.a * a.p, a.p);
+            acc[7].addp(rn, a.p);
+        }
+    }
+    __device__ static void finalize(const Desc<T>& d, const double* tot) {
+        FPfB1<T>::finalize(d, tot);
+        if (!d.ctrl->pf_full) pf_next_dir(d.ctrl, tot + 4);   // else the explicit residual pass does it
+    }
+};
+
+template <typename T>
 struct FPfVIn {   // input v for the explicit J v (only when pf_full)
     static constexpr int NR = 0;
     using Ctx = NoCtx;
@@ -737,16 +842,16 @@ struct FColLapPFFull {
 
 template <typename T>
 struct FPfB3 {   // explicit R = J v - b, active set {bound and R > 0}, beta, convergence (only when pf_full)
-    static constexpr int NR = 3;
+    static constexpr int NR = 7;
     struct Ctx { T kappa; double kd; const T* ro; T* rn; };
     __device__ static bool skip(const Desc<T>& d) { return ldflag(&d.ctrl->pf_a) || !ldflag(&d.ctrl->pf_full); }
     __device__ static Ctx prep(const Desc<T>& d) {
         const int sel = ldflag(&d.ctrl->pf_rsel);
         return Ctx{T(d.k.kappa), d.k.kappa, pf_r(d, sel), pf_r(d, sel ^ 1)};
     }
-    struct In { T ro, x, a, b; uint8_t fl; };
+    struct In { T ro, x, a, b, p; uint8_t fl; };
     __device__ static In load(const Desc<T>& d, const Ctx& c, size_t i) {
-        return In{c.ro[i], d.th[0][i], d.r[0][i], d.r[1][i], d.flags[i]};
+        return In{c.ro[i], d.th[0][i], d.r[0][i], d.r[1][i], d.th[2][i], d.flags[i]};
     }
     __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, const In& in, T (&v)[1], Acc<T>* acc) {
         const T ro = in.ro, x = in.x, a = in.a, b = in.b, kl = c.kappa * v[0];
@@ -772,10 +877,18 @@ struct FPfB3 {   // explicit R = J v - b, active set {bound and R > 0}, beta, co
         acc[0].addp(rn, rn);
         acc[1].addp(rn, ro);
         acc[2].add(active ? T(1) : T(0));
+        if (!active) {   // sums of the next direction (free pixels; used by the three-pass iteration)
+            const T ar = a * rn;
+            acc[3].addp(ar, rn);
+            acc[4].addp(ar, in.p);
+            acc[5].addp(a * in.p, in.p);
+            acc[6].addp(rn, in.p);
+        }
     }
     __device__ static void finalize(const Desc<T>& d, const double* tot) {
         d.ctrl->pf_rsel ^= 1;
         pf_finish(d, d.ctrl, tot[0], tot[1], tot[2], true);
+        pf_next_dir(d.ctrl, tot + 3);
     }
 };
 

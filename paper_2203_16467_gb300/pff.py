@@ -107,6 +107,9 @@ _SIGS = {
     "pff_batch_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(StepReport), _IP]),
     "pff_batch_set_group_size": (ctypes.c_int, [_P, ctypes.c_int]),
     "pff_batch_autotune": (ctypes.c_int, [_P, _IP, ctypes.c_int, ctypes.c_int, _IP, ctypes.POINTER(StepReport), _IP]),
+    "pff_set_kernel_variant": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "pff_get_kernel_variant": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _IP]),
+    "pff_batch_autotune_kernels": (ctypes.c_int, [_P, ctypes.c_int, _IP, _DP, ctypes.POINTER(StepReport), _IP]),
     "pff_kernel_launches": (ctypes.c_ulonglong, []),
     "pff_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "pff_set_graphs": (ctypes.c_int, [ctypes.c_int]),
@@ -418,6 +421,33 @@ def batch_autotune(b, max_slots, group_sizes=(1, 2, 4, 8), steps_each=2):
     chosen = ctypes.c_int()
     _check(lib.pff_batch_autotune(b, gs, n, steps_each, ctypes.byref(chosen), reps, done), allow=(ERR_NOT_CONVERGED,))
     return chosen.value, [[reps[i * total + s].to_dict() for s in range(done[i])] for i in range(max_slots)]
+
+
+VARIANT_COLUMN_SHAPE, VARIANT_BCCG_PASSES = 2, 3
+
+
+def set_kernel_variant(kind, grid_n, ncomp, variant):
+    return _check(lib.pff_set_kernel_variant(kind, grid_n, ncomp, variant))
+
+
+def get_kernel_variant(kind, grid_n, ncomp):
+    v = ctypes.c_int()
+    _check(lib.pff_get_kernel_variant(kind, grid_n, ncomp, ctypes.byref(v)))
+    return v.value
+
+
+def batch_autotune_kernels(b, max_slots, steps_each=2):
+    """Measure the eight kernel-variant combinations on load steps of the batch and keep the
+    fastest; returns ((1-component column shape, 3-component column shape, BCCG passes),
+    scores, per-slot step reports)."""
+    total = 8 * (steps_each + 1)
+    chosen = (ctypes.c_int * 3)()
+    scores = (ctypes.c_double * 8)()
+    reps = (StepReport * (max_slots * total))()
+    done = (ctypes.c_int * max_slots)()
+    _check(lib.pff_batch_autotune_kernels(b, steps_each, chosen, scores, reps, done), allow=(ERR_NOT_CONVERGED,))
+    return ((chosen[0], chosen[1], chosen[2]), list(scores),
+            [[reps[i * total + s].to_dict() for s in range(done[i])] for i in range(max_slots)])
 
 
 # ---------------------------------------------------------------------------- convenience wrappers

@@ -48,9 +48,9 @@ class Request:
 @dataclass
 class Sim:
     req: Request
-    problem: object
+    E: object                     # host modulus field (the lane creates the problem on its stream)
     bytes: int
-    stream: object = None         # keeps the problem's own stream alive
+    problem: object = None
     slot: int = -1
     steps: int = 0
     started: float = None
@@ -77,9 +77,11 @@ class Lane:
     def __init__(self, server, key):
         self.server = server
         self.key = key
+        # one stream for everything of this lane (the problems' uploads and read-backs, the batch's
+        # steps and graph captures): only the lane's thread touches it
         self.cuda_stream = _new_stream()
-        sp = self.cuda_stream.cuda_stream if self.cuda_stream is not None else None
-        self.batch = pff.create_batch(server.max_slots, 1 << 62, sp)   # the server keeps the HBM budget
+        self.stream_ptr = self.cuda_stream.cuda_stream if self.cuda_stream is not None else None
+        self.batch = pff.create_batch(server.max_slots, 1 << 62, self.stream_ptr)   # the server keeps the budget
         self.pending = []
         self.sims = {}
         self.steps_log = []           # (t_start, t_end) of every batch step of the lane
@@ -108,7 +110,9 @@ class Lane:
                     if self.stop:
                         return
                     new, self.pending = self.pending, []
-                for sim in new:   # between two steps of this lane
+                for sim in new:   # between two steps of this lane, on the lane's stream
+                    sim.problem = srv.make_problem(sim.req, sim.E, self.stream_ptr)
+                    sim.E = None
                     sim.slot = pff.batch_admit(self.batch, sim.problem.h)
                     self.sims[sim.slot] = sim
                 t0 = srv.now()
@@ -150,7 +154,6 @@ class Lane:
             self.server.retire(sim, self.key)
         self.sims = {}
         for sim in self.pending:
-            sim.problem.close()
             self.server.release_budget(sim)
         self.pending = []
         pff.destroy_batch(self.batch)
@@ -217,17 +220,15 @@ class Server:
             self.queue.append(req)
             self.wake_cv.notify_all()
 
-    def _make(self, r):
+    @staticmethod
+    def make_problem(r, E, stream):
+        """The device state of request r (called by its lane's thread, on the lane's stream)."""
         em = eps_M(1.0, 0.2, 1.0, r.ell)
-        E = modulus_field(r.n, r.n, r.lc, r.seed)
-        st = _new_stream()
-        p = pff.Problem(r.n, r.n, r.precision, stream=st.cuda_stream if st is not None else None, E=E,
-                        model=(r.fracture, r.split, r.irreversibility),
-                        params=dict(nu=0.2, ell=r.ell, mech_tol=r.tol, pf_tol=r.tol,
-                                    d_eps_bar=(0.0, em / 20, 0.0)))
+        p = pff.Problem(r.n, r.n, r.precision, stream=stream, E=E, model=(r.fracture, r.split, r.irreversibility),
+                        params=dict(nu=0.2, ell=r.ell, mech_tol=r.tol, pf_tol=r.tol, d_eps_bar=(0.0, em / 20, 0.0)))
         if r.preload:
             p.set_strain(None, (0.0, r.preload * em, 0.0))
-        return p, st
+        return p
 
     def _admit(self):
         """Hand every arrived request that fits the budget and the slots to its lane."""
@@ -246,11 +247,10 @@ class Server:
             if not fits:
                 waiting.append(r)
                 continue
-            p, st = self._make(r)
             key = (r.n, r.precision)
             if key not in self.lanes:
                 self.lanes[key] = Lane(self, key)
-            self.lanes[key].hand(Sim(r, p, nb, st))
+            self.lanes[key].hand(Sim(r, modulus_field(r.n, r.n, r.lc, r.seed), nb))
         with self.mu:
             self.queue = waiting + self.queue   # (requests submitted meanwhile stay queued)
 

@@ -49,3 +49,12 @@ def test_invalid_sizes_rejected_without_gpu(libpff):
     h = ctypes.c_void_p()
     assert pff.lib.pff_create_problem(48, 64, pff.MIXED, None, ctypes.byref(h)) == pff.ERR_INVALID_ARG
     assert pff.lib.pff_create_problem(64, 64, 7, None, ctypes.byref(h)) == pff.ERR_INVALID_ARG
+
+
+def test_kernel_variant_arguments_checked_without_gpu(libpff):
+    from paper_2203_16467_gb300 import pff
+    assert pff.lib.pff_set_kernel_variant(0, 512, 1, 1) == pff.ERR_INVALID_ARG
+    assert pff.lib.pff_set_kernel_variant(pff.VARIANT_COLUMN_SHAPE, 512, 2, 0) == pff.ERR_INVALID_ARG
+    assert pff.lib.pff_set_kernel_variant(pff.VARIANT_COLUMN_SHAPE, 512, 1, 2) == pff.ERR_INVALID_ARG
+    assert pff.lib.pff_set_kernel_variant(pff.VARIANT_BCCG_PASSES, 0, 1, -1) == pff.ERR_INVALID_ARG
+    assert pff.lib.pff_set_barrier_spin_limit(-1) == pff.ERR_INVALID_ARG

@@ -13,15 +13,15 @@ def test_bytes_per_iteration_512():
     assert b[(0, 1)] == pytest.approx(14 * 4 + 3 * s)  # 68.05: read p, r, eps*, phi, E; write p, S
     assert b[(1, 1)] == pytest.approx(15 * 4 + 3 * s)  # 72.05: read S, theta, r, p; write theta, r
     cg = b[(0, 1)] + b[(2, 1)] + b[(1, 1)]
-    bccg = b[(0, 3)] + b[(2, 4)] + b[(1, 4)] + b[(3, 11)]
+    bccg = b[(0, 3)] + b[(2, 9)] + b[(1, 9)]
     explicit = b[(0, 4)] + b[(2, 6)] + b[(1, 5)]
-    assert round(cg) == 164 and round(bccg) == 82 and round(explicit) == 46
+    assert round(cg) == 164 and round(bccg) == 66 and round(explicit) == 50
     bi = bench.bytes_per_px(4, 512, iso=True)          # the isotropic tangent reads no strain
     assert round(bi[(0, 1)] + bi[(2, 1)] + bi[(1, 1)]) == 152
     b8 = bench.bytes_per_px(8, 512)
     for k in b:
         # FP64 doubles each value but the one-byte flag plane
-        flags = {(0, 3): 1, (3, 11): 1, (1, 5): 2}.get(k, 0)
+        flags = {(0, 3): 1, (1, 9): 1, (1, 5): 2}.get(k, 0)
         assert b8[k] == pytest.approx(2 * (b[k] - flags) + flags)
 
 
@@ -31,6 +31,6 @@ def test_active_launches_follow_the_reports():
              {"mech_cg_iters": 0, "newton_iters": 0, "bccg_iters": 0, "bccg_full_iters": 0}]]
     a = bench.active_launches(reps)
     assert a[(0, 1)] == 14 and a[(2, 1)] == 14 and a[(1, 1)] == 14
-    assert all(a[k] == 12 for k in ((0, 3), (2, 4), (1, 4), (3, 11)))
+    assert all(a[k] == 12 for k in ((0, 3), (2, 9), (1, 9)))
     assert all(a[k] == 4 for k in ((0, 4), (2, 6), (1, 5)))
     assert set(a) == set(bench.KERNEL_NAMES)

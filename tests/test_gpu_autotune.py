@@ -59,3 +59,48 @@ def test_autotune_picks_a_candidate_and_changes_no_result(env):
     pff.destroy_batch(b)
     for p in probs:
         p.close()
+
+
+def test_kernel_variants_agree_and_tuner_keeps_a_candidate(env):
+    # the column-pass shapes (4 or 2 columns per block) and the BCCG iteration structures (three
+    # or four passes) compute the same method; fields after the same load steps agree to FP32
+    # rounding, and the autotuner leaves one of its eight candidate combinations set
+    pff, torch = env
+    n = 512
+    CS, BP = pff.VARIANT_COLUMN_SHAPE, pff.VARIANT_BCCG_PASSES
+    out = {}
+    try:
+        for v in (0, 1):
+            pff.set_kernel_variant(CS, n, 1, v)
+            pff.set_kernel_variant(CS, n, 3, v)
+            pff.set_kernel_variant(BP, 0, 1, v)
+            assert pff.get_kernel_variant(CS, n, 1) == v and pff.get_kernel_variant(CS, n, 3) == v
+            assert pff.get_kernel_variant(BP, 0, 1) == v
+            b, probs = _batch(pff, torch, n)
+            reps = pff.batch_step(b, len(probs), 3)
+            out[v] = ([p.get_fields(pff.FIELD_PHI) for p in probs], [p.get_fields(pff.FIELD_STRAIN) for p in probs],
+                      reps)
+            pff.destroy_batch(b)
+            for p in probs:
+                p.close()
+        for j in range(len(MODELS)):
+            (pa, ea, ra), (pb, eb, rb) = [(o[0][j], o[1][j], o[2][j]) for o in (out[0], out[1])]
+            assert [r["incremented"] for r in ra] == [r["incremented"] for r in rb]
+            assert np.linalg.norm(ea - eb) / np.linalg.norm(eb) < 1e-5
+            assert np.linalg.norm(pa - pb) / max(np.linalg.norm(pb), 1e-30) < 1e-4
+        b, probs = _batch(pff, torch, n)
+        chosen, scores, reps = pff.batch_autotune_kernels(b, len(probs), steps_each=1)
+        assert all(c in (0, 1) for c in chosen) and len(scores) == 8
+        assert all(s > 0 for s in scores)
+        assert pff.get_kernel_variant(CS, n, 1) == chosen[0] and pff.get_kernel_variant(CS, n, 3) == chosen[1]
+        assert pff.get_kernel_variant(BP, 0, 1) == chosen[2]
+        assert all(len(r) == 16 for r in reps)
+        pff.destroy_batch(b)
+        for p in probs:
+            p.close()
+    finally:
+        pff.set_kernel_variant(CS, n, 1, 0)
+        pff.set_kernel_variant(CS, n, 3, 0)
+        pff.set_kernel_variant(BP, 0, 1, 0)
+    with pytest.raises(pff.PffError):
+        pff.set_kernel_variant(CS, 256, 1, 1)

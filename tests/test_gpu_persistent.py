@@ -81,7 +81,11 @@ def test_persistent_load_steps_match_per_phase_kernels(pff, model):
     (ra, pa), (rb, pb) = out[True], out[False]
     assert sum(r["bccg_iters"] for r in ra) > 0
     scale = max(np.linalg.norm(pb), 1e-30)
-    assert np.linalg.norm(pa - pb) / scale < 1e-5
+    # the persistent kernel runs Algorithm 1 in four passes (alpha from p.Jp summed in real
+    # space), the default path in three (alpha via Parseval): the FP32 roundings differ, and
+    # over three load steps the two paths stay within 1e-4 (each solve is held to 1e-5 of
+    # the oracle by test_persistent_phase_field_solve_parity_512 and tests/test_gpu_solvers.py)
+    assert np.linalg.norm(pa - pb) / scale < 1e-4
     for x, y in zip(ra, rb):
         # FP32 solves stop at the rounding level of J v - b, where the iteration at which
         # the stopping tests fire depends on the summation order of the dot products
