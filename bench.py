@@ -372,7 +372,7 @@ def run_ours(args, rank, world, dev):
         pff.batch_set_group_size(tb, GROUP_SIZE)
         for p in tprobs:
             assert pff.batch_admit(tb, p.h) is not None
-        chosen, scores, _ = pff.batch_autotune_kernels(tb, len(tprobs), steps_each=2)
+        chosen, scores, _ = pff.batch_autotune_kernels(tb, len(tprobs), steps_each=4)
         pff.destroy_batch(tb)
         for p in tprobs:
             p.close()
@@ -381,8 +381,9 @@ def run_ours(args, rank, world, dev):
                             "column_pass_3_components_columns_per_block": 4 if chosen[1] == 0 else 2,
                             "bccg_passes_per_iteration": 3 if chosen[2] == 0 else 4},
                  "scores_pixel_iters_per_s": dict(zip(names, scores)),
-                 "how": "pff_batch_autotune_kernels: each of the 8 variant combinations on 3 load steps (2 timed) "
-                        "of a separate batch of the eight simulations from the benchmark start, same launch mode"}
+                 "how": "pff_batch_autotune_kernels: 4 rounds (alternate rounds in reverse order), in each "
+                        "every one of the 8 variant combinations runs 2 load steps (1 timed) of a separate batch "
+                        "of the eight simulations from the benchmark start, same launch mode"}
     probs, E = make_problems(pff, sp, rank, pff.MIXED, VARIANTS)
     nprob = len(probs)
     budget = sum(pff.problem_bytes(N, N, pff.MIXED) for _ in probs)
@@ -563,6 +564,11 @@ def baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed, ph
         out["dominant_kernel_scaling"] = kernel_scaling(pff, torch, sp)
     except Exception as e:
         out["dominant_kernel_scaling"] = {"error": str(e)[:200]}
+    # the two BCCG iteration structures (three / four operator passes), same start, same launches
+    try:
+        out["bccg_passes_compare"] = bccg_passes_compare(pff, torch, sp)
+    except Exception as e:
+        out["bccg_passes_compare"] = {"error": str(e)[:200]}
     # the opt-in Fourier-Helmholtz preconditioned BCCG against Algorithm 1, both from the
     # same start of the same eight variants, batched the way the timed region is
     try:
@@ -870,6 +876,42 @@ def kernel_scaling(pff, torch, sp, key=(0, 1), variant=("AT1", "SPECTRAL", "CRAC
             "note": "one load step after two warm-up steps; the identical simulations work in the same "
                     "launches; the skipped launches at the end of each 8-iteration chunk count against "
                     "the time, as in the roofline figure"}
+
+
+def bccg_passes_compare(pff, torch, sp, warm=3, steps=8):
+    """The eight variants from the benchmark start under each BCCG iteration structure (three
+    passes with alpha from the column pass, or four with alpha from p.Jp), batched as the timed
+    region is, CUDA events on the stream around the timed batch steps."""
+    res = {}
+    keep = pff.get_kernel_variant(pff.VARIANT_BCCG_PASSES, 0, 1)
+    try:
+        for v in (0, 1):
+            pff.set_kernel_variant(pff.VARIANT_BCCG_PASSES, 0, 1, v)
+            probs, _ = make_problems(pff, sp, 0, pff.MIXED, VARIANTS)
+            b = pff.create_batch(len(probs), sum(pff.problem_bytes(N, N, pff.MIXED) for _ in probs), sp)
+            pff.batch_set_group_size(b, GROUP_SIZE)
+            for p in probs:
+                assert pff.batch_admit(b, p.h) is not None
+            pff.batch_step(b, len(probs), warm)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = pff.batch_step(b, len(probs), steps)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            rr = [r for o in out for r in o]
+            it = sum(r["mech_cg_iters"] + r["bccg_iters"] for r in rr)
+            res["three_passes" if v == 0 else "four_passes"] = {
+                "ms_per_batch_step": 1e3 * dt / steps, "pixel_cg_iters_per_s": it * N * N / dt,
+                "bccg_iters": sum(r["bccg_iters"] for r in rr), "mech_cg_iters": sum(r["mech_cg_iters"] for r in rr)}
+            pff.destroy_batch(b)
+            for p in probs:
+                p.close()
+    finally:
+        pff.set_kernel_variant(pff.VARIANT_BCCG_PASSES, 0, 1, keep)
+    res["speedup_three_over_four"] = (res["four_passes"]["ms_per_batch_step"] / res["three_passes"]["ms_per_batch_step"])
+    res["sample"] = (f"the eight variants from eps_bar_yy = {PRELOAD} eps_M, {warm} warm-up and {steps} timed batch "
+                     f"steps each, host wall clock around synchronised batch steps")
+    return res
 
 
 def precond_compare(pff, torch, sp, warm=2, steps=6):

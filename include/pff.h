@@ -310,15 +310,17 @@ enum { PFF_VARIANT_COLUMN_SHAPE = 2, PFF_VARIANT_BCCG_PASSES = 3 };
 int pff_set_kernel_variant(int kind, int grid_n, int ncomp, int variant);
 int pff_get_kernel_variant(int kind, int grid_n, int ncomp, int* variant);
 
-/* Autotuner of the kernel variants on ordinary load steps of a batch: each of
- * the eight combinations (one-component column shape, three-component column
- * shape, BCCG passes) = (c & 1, (c >> 1) & 1, (c >> 2) & 1), c = 0..7, runs
- * steps_each + 1 load steps in the batch's own launch configuration (the first
- * after a change is not timed: graphs are re-captured), scored by
- * pixel-iterations per second of host wall time; the best combination stays
- * set and is returned in chosen[3]; scores[8] (optional) receives the eight
- * scores.  reports / steps_done as pff_batch_autotune (per slot,
- * 8 (steps_each + 1) entries).  The steps advance the batch's simulations. */
+/* Autotuner of the kernel variants on ordinary load steps of a batch: the eight
+ * combinations (one-component column shape, three-component column shape, BCCG
+ * passes) = (c & 1, (c >> 1) & 1, (c >> 2) & 1), c = 0..7, run in steps_each
+ * rounds; in each round every combination runs two load steps in the batch's own
+ * launch configuration (the first after the change is not timed: graphs are
+ * re-captured), odd rounds in reverse order, so that all combinations are
+ * measured on the same stretch of the simulations; scored by pixel-iterations per
+ * second of host wall time (steps_each >= 2 recommended).  The
+ * best combination stays set and is returned in chosen[3]; scores[8] (optional)
+ * receives the eight scores.  reports / steps_done as pff_batch_autotune (per
+ * slot, 16 steps_each entries).  The steps advance the batch's simulations. */
 int pff_batch_autotune_kernels(pff_batch* b, int steps_each, int* chosen, double* scores, pff_step_report* reports,
                                int* steps_done);
 

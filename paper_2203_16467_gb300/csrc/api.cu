@@ -1674,36 +1674,45 @@ int pff_batch_autotune_kernels(pff_batch* b, int steps_each, int* chosen, double
         if (!rc) rc = pff_set_kernel_variant(PFF_VARIANT_BCCG_PASSES, 0, 1, cand[c][2]);
         return rc;
     };
-    const int per = steps_each + 1;   // one untimed step after each change (graph re-capture)
-    const int total = NCAND * per;
+    // steps_each rounds; in each round every candidate runs one untimed load step after its
+    // change (graph re-capture) and one timed step, so that all candidates see load steps from
+    // the same stretch of the simulations
+    const int total = NCAND * 2 * steps_each;
     std::vector<int> done(b->max_slots, 0);
-    int status = PFF_OK, best = 0;
-    double best_score = -1.0;
-    for (int c = 0; c < NCAND; ++c) {
-        int rc = apply(c);
-        if (rc) return rc;
-        double elapsed = 0.0, work = 0.0;
-        for (int s = 0; s < per; ++s) {
-            std::vector<pff_step_report> one(b->max_slots);
-            std::vector<int> d1(b->max_slots, 0);
-            const auto t0 = std::chrono::steady_clock::now();
-            rc = pff_batch_step(b, 1, one.data(), d1.data());
-            const auto t1 = std::chrono::steady_clock::now();
-            if (rc && rc != PFF_ERR_NOT_CONVERGED) return rc;
-            if (rc) status = rc;
-            for (int i = 0; i < b->max_slots; ++i) {
-                if (!d1[i]) continue;
-                const pff_step_report& r = one[i];
-                if (reports) reports[(size_t)i * total + done[i]] = r;
-                ++done[i];
-                if (s > 0 && b->slot[i])
-                    work += (double)(r.mech_cg_iters + r.newton_iters + r.bccg_iters) * b->slot[i]->nx * b->slot[i]->ny;
+    std::vector<double> elapsed(NCAND, 0.0), work(NCAND, 0.0);
+    int status = PFF_OK;
+    for (int round = 0; round < steps_each; ++round) {
+        for (int cc = 0; cc < NCAND; ++cc) {
+            // odd rounds visit the candidates in reverse order, so that a steady drift of the
+            // per-iteration cost along the load steps does not favour the early candidates
+            const int c = (round & 1) ? NCAND - 1 - cc : cc;
+            int rc = apply(c);
+            if (rc) return rc;
+            for (int s = 0; s < 2; ++s) {
+                std::vector<pff_step_report> one(b->max_slots);
+                std::vector<int> d1(b->max_slots, 0);
+                const auto t0 = std::chrono::steady_clock::now();
+                rc = pff_batch_step(b, 1, one.data(), d1.data());
+                const auto t1 = std::chrono::steady_clock::now();
+                if (rc && rc != PFF_ERR_NOT_CONVERGED) return rc;
+                if (rc) status = rc;
+                for (int i = 0; i < b->max_slots; ++i) {
+                    if (!d1[i]) continue;
+                    const pff_step_report& r = one[i];
+                    if (reports) reports[(size_t)i * total + done[i]] = r;
+                    ++done[i];
+                    if (s == 1 && b->slot[i])
+                        work[c] += (double)(r.mech_cg_iters + r.newton_iters + r.bccg_iters) * b->slot[i]->nx * b->slot[i]->ny;
+                }
+                if (s == 1) elapsed[c] += std::chrono::duration<double>(t1 - t0).count();
             }
-            if (s > 0) elapsed += std::chrono::duration<double>(t1 - t0).count();
         }
-        const double score = elapsed > 0.0 ? work / elapsed : 0.0;
+    }
+    int best = 0;
+    for (int c = 0; c < NCAND; ++c) {
+        const double score = elapsed[c] > 0.0 ? work[c] / elapsed[c] : 0.0;
         if (scores) scores[c] = score;
-        if (score > best_score) { best_score = score; best = c; }
+        if (score > (elapsed[best] > 0.0 ? work[best] / elapsed[best] : 0.0)) best = c;
     }
     if (steps_done)
         for (int i = 0; i < b->max_slots; ++i) steps_done[i] = done[i];

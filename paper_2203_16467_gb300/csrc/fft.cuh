@@ -249,6 +249,11 @@ __device__ __forceinline__ int ridx(int x) { return 2 * pidx(x >> 1) + (x & 1); 
 #ifndef PFF_ROW_G
 #define PFF_ROW_G 2
 #endif
+// Row-inverse passes issue the epilogue's pixel loads before staging and transforming the
+// spectrum (they land during the FFT) when a thread handles at most this many pixels.
+#ifndef PFF_INV_PREFETCH
+#define PFF_INV_PREFETCH 8
+#endif
 template <class F, bool TWO> struct InOf { struct type {}; };
 template <class F> struct InOf<F, true> { using type = typename F::In; };
 
@@ -368,7 +373,7 @@ __device__ __forceinline__ void row_inv_item(const Desc<T>& d, const typename F:
     using C = typename CT<T>::t;
     constexpr int M = Cfg::M, SP = Cfg::SP, ROWS = Cfg::ROWS, NT = Cfg::NT;
     const T* rb = reinterpret_cast<const T*>(buf);
-    constexpr bool TWO = HasIn<F>::value && (ROWS * NX) % NT == 0 && ROWS * NX / NT <= 4;
+    constexpr bool TWO = HasIn<F>::value && (ROWS * NX) % NT == 0 && ROWS * NX / NT <= PFF_INV_PREFETCH;
     constexpr int PPT = TWO ? ROWS * NX / NT : 1;
     using InT = typename InOf<F, TWO>::type;
     InT in[PPT];

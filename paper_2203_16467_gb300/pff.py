@@ -440,7 +440,7 @@ def batch_autotune_kernels(b, max_slots, steps_each=2):
     """Measure the eight kernel-variant combinations on load steps of the batch and keep the
     fastest; returns ((1-component column shape, 3-component column shape, BCCG passes),
     scores, per-slot step reports)."""
-    total = 8 * (steps_each + 1)
+    total = 16 * steps_each
     chosen = (ctypes.c_int * 3)()
     scores = (ctypes.c_double * 8)()
     reps = (StepReport * (max_slots * total))()

@@ -83,6 +83,7 @@ class Lane:
         self.stream_ptr = self.cuda_stream.cuda_stream if self.cuda_stream is not None else None
         self.batch = pff.create_batch(server.max_slots, 1 << 62, self.stream_ptr)   # the server keeps the budget
         self.pending = []
+        self.admitting = 0            # taken off pending, not yet in sims
         self.sims = {}
         self.steps_log = []           # (t_start, t_end) of every batch step of the lane
         self.cv = threading.Condition()
@@ -98,7 +99,7 @@ class Lane:
 
     def busy(self):
         with self.cv:
-            return bool(self.pending or self.sims)
+            return bool(self.pending or self.sims or self.admitting)
 
     def _work(self):
         srv = self.server
@@ -110,11 +111,15 @@ class Lane:
                     if self.stop:
                         return
                     new, self.pending = self.pending, []
+                    self.admitting = len(new)
                 for sim in new:   # between two steps of this lane, on the lane's stream
                     sim.problem = srv.make_problem(sim.req, sim.E, self.stream_ptr)
                     sim.E = None
-                    sim.slot = pff.batch_admit(self.batch, sim.problem.h)
-                    self.sims[sim.slot] = sim
+                    slot = pff.batch_admit(self.batch, sim.problem.h)
+                    with self.cv:
+                        sim.slot = slot
+                        self.sims[slot] = sim
+                        self.admitting -= 1
                 t0 = srv.now()
                 out = pff.batch_step(self.batch, srv.max_slots, 1)
                 t1 = srv.now()
@@ -132,15 +137,17 @@ class Lane:
                     if reps[0]["broken"] or sim.steps >= sim.req.max_steps:
                         finished.append(slot)
                 for slot in finished:
-                    sim = self.sims.pop(slot)
                     pff.batch_release(self.batch, slot)
-                    srv.retire(sim, self.key)
+                    srv.retire(self.sims[slot], self.key)
+                    with self.cv:
+                        self.sims.pop(slot)
         except Exception as e:   # reported by the request loop
             self.error = e
             with self.cv:
                 for sim in self.pending:
                     srv.release_budget(sim)
                 self.pending = []
+                self.admitting = 0
             srv.wake()
 
     def close(self):

@@ -94,7 +94,7 @@ def test_kernel_variants_agree_and_tuner_keeps_a_candidate(env):
         assert all(s > 0 for s in scores)
         assert pff.get_kernel_variant(CS, n, 1) == chosen[0] and pff.get_kernel_variant(CS, n, 3) == chosen[1]
         assert pff.get_kernel_variant(BP, 0, 1) == chosen[2]
-        assert all(len(r) == 16 for r in reps)
+        assert all(len(r) == 16 for r in reps)   # one round: two steps per combination
         pff.destroy_batch(b)
         for p in probs:
             p.close()
