@@ -307,28 +307,36 @@ def bytes_per_px(es, nx, iso=False):
         (0, 4): es + s_pc,                     # explicit J v only: read v; write S
         (2, 6): 2 * s_pc,                      # explicit J v only: column pass Laplacian of v
         (1, 5): 7 * es + s_pc + 2,             # explicit residual only: read S,r,v,a,b,p,flag; write R,r,flag
+        # the four-pass BCCG iteration (kernel variant): the direction pass (0, 3) as above, then
+        (2, 4): 2 * s_pc,                      # column pass Laplacian of p
+        (1, 4): 4 * es + s_pc,                 # J p, p.Jp, r.p: read S,p,a,r; write Jp
+        (3, 11): 9 * es + 1,                   # iterate: read v,p,v_con,R,Jp,r; write v,R,r',flag
     }
 
 
 KERNEL_NAMES = {(0, 1): "row_fwd_cg", (2, 1): "col_gamma_cg", (1, 1): "row_inv_cg", (0, 3): "row_fwd_bccg_dir",
                 (2, 9): "col_lap_bccg_dir", (1, 9): "row_inv_bccg_iter",
-                (0, 4): "row_fwd_bccg_v", (2, 6): "col_lap_bccg_v", (1, 5): "row_inv_bccg_explicit"}
+                (0, 4): "row_fwd_bccg_v", (2, 6): "col_lap_bccg_v", (1, 5): "row_inv_bccg_explicit",
+                (2, 4): "col_lap_bccg_dir_4pass", (1, 4): "row_inv_bccg_Jp_4pass", (3, 11): "elem_bccg_iter_4pass"}
+BCCG3 = ((2, 9), (1, 9))            # the default three-pass iteration's own classes
+BCCG4 = ((2, 4), (1, 4), (3, 11))   # the four-pass iteration's own classes
 
 
-def kernel_bytes(reps_per_problem, isos, es, nx, ny):
+def kernel_bytes(reps_per_problem, isos, es, nx, ny, bccg4=False):
     """Algorithmic bytes of each kernel class summed over the problems' working launches."""
     out = {k: 0.0 for k in KERNEL_NAMES}
     for reps, iso in zip(reps_per_problem, isos):
-        a = active_launches([reps])
+        a = active_launches([reps], bccg4)
         b = bytes_per_px(es, nx, iso)
         for k in out:
             out[k] += a[k] * b[k] * nx * ny
     return out
 
 
-def active_launches(reps_per_problem):
+def active_launches(reps_per_problem, bccg4=False):
     """Problem-launches of each kernel class that do work, from the per-step iteration counts
-    (the explicit-residual chain works only in iterations that evaluate J v explicitly)."""
+    (the explicit-residual chain works only in iterations that evaluate J v explicitly; bccg4:
+    the BCCG iterations ran as four passes)."""
     cnt = {k: 0 for k in KERNEL_NAMES}
     for reps in reps_per_problem:
         for r in reps:
@@ -336,7 +344,7 @@ def active_launches(reps_per_problem):
             cnt[(0, 1)] += cg
             cnt[(2, 1)] += cg
             cnt[(1, 1)] += cg
-            for k in ((0, 3), (2, 9), (1, 9)):
+            for k in ((0, 3),) + (BCCG4 if bccg4 else BCCG3):
                 cnt[k] += pf
             for k in ((0, 4), (2, 6), (1, 5)):
                 cnt[k] += full
@@ -435,8 +443,9 @@ def run_ours(args, rank, world, dev):
     bccg = sum(r["bccg_iters"] for rr in reps for r in rr)
     nsteps_done = sum(len(rr) for rr in reps)
     # kernel-class timing (live, CUDA events on the batch stream)
+    bccg4 = pff.get_kernel_variant(pff.VARIANT_BCCG_PASSES, N, 1) == 1
     kt = {k: pff.timing_read(*k) for k in KERNEL_NAMES}
-    kb = kernel_bytes(reps_k, [v[1] == "ISOTROPIC" for v in VARIANTS], 4, N, N)
+    kb = kernel_bytes(reps_k, [v[1] == "ISOTROPIC" for v in VARIANTS], 4, N, N, bccg4)
     kernels = {}
     for k, name in KERNEL_NAMES.items():
         ms, nl = kt[k]
@@ -450,7 +459,7 @@ def run_ours(args, rank, world, dev):
     dom = max(kernels, key=lambda n: kernels[n]["ms"])
     # the whole path in the timed launch mode: algorithmic bytes of every kernel class over the
     # timed region (iteration counts of its own reports) per unit of its wall time
-    timed_bytes = sum(kernel_bytes(reps, [v[1] == "ISOTROPIC" for v in VARIANTS], 4, N, N).values())
+    timed_bytes = sum(kernel_bytes(reps, [v[1] == "ISOTROPIC" for v in VARIANTS], 4, N, N, bccg4).values())
     # distributed aggregation: max time, summed work (no data-path collective)
     elapsed_max, (mech_all, bccg_all, steps_all) = aggregate(elapsed, [mech, bccg, nsteps_done], world,
                                                              f"cuda:{dev}")
@@ -632,7 +641,8 @@ def baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed, ph
 
 def kernel_table(pff, reps_per_problem, nx, ny, iso=False):
     """Per kernel class: time (CUDA events around each launch), launches, algorithmic GB/s."""
-    kb = kernel_bytes(reps_per_problem, [iso] * len(reps_per_problem), 4, nx, ny)
+    bccg4 = pff.get_kernel_variant(pff.VARIANT_BCCG_PASSES, nx, 1) == 1
+    kb = kernel_bytes(reps_per_problem, [iso] * len(reps_per_problem), 4, nx, ny, bccg4)
     out = {}
     for k, name in KERNEL_NAMES.items():
         ms, nl = pff.timing_read(*k)
@@ -645,9 +655,6 @@ def kernel_table(pff, reps_per_problem, nx, ny, iso=False):
 def roofline_of(kernels):
     peak, kind = hbm_peak()
     dom = max(kernels, key=lambda n: kernels[n]["ms"])
-    # the whole path in the timed launch mode: algorithmic bytes of every kernel class over the
-    # timed region (iteration counts of its own reports) per unit of its wall time
-    timed_bytes = sum(kernel_bytes(reps, [v[1] == "ISOTROPIC" for v in VARIANTS], 4, N, N).values())
     ach = kernels[dom]["achieved_GBs"]
     return {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
             "frac": ach / peak if ach else None, "peak_kind": kind}
@@ -866,7 +873,7 @@ def kernel_scaling(pff, torch, sp, key=(0, 1), variant=("AT1", "SPECTRAL", "CRAC
         pff.destroy_batch(b)
         for p in probs:
             p.close()
-        act = active_launches(out)[key]          # problem-launches that did work
+        act = active_launches(out, pff.get_kernel_variant(pff.VARIANT_BCCG_PASSES, N, 1) == 1)[key]   # working
         work = act // k                           # launches with all k simulations working
         gbs = act * bpp * N * N / (ms * 1e-3) / 1e9 if ms > 0 else None
         rows.append({"simulations_per_launch": k, "launches": nl, "working_launches": work,

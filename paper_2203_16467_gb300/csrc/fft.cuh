@@ -199,9 +199,9 @@ struct RowCfg {
     static constexpr int SP = padded_len(M) + 2;            // pitch (complex): padded M values + slot for k = M
     static constexpr int NSEQ = NC * ROWS;
     // twiddles staged in shared memory: length-M FFT table (padded indices) + the
-    // M+1 real-FFT factors
+    // real-FFT factors exp(-2 pi i k / NX), k < M/2 (the split handles k and M - k together)
     static constexpr int TWF = padded_len(M);
-    static constexpr int TWS = TWF + M + 1;
+    static constexpr int TWS = TWF + M / 2;
     static constexpr size_t SMEM = (size_t)(NSEQ * SP + TWS) * sizeof(typename CT<T>::t);
 };
 
@@ -307,29 +307,39 @@ __device__ __forceinline__ void row_fwd_fft_store(const Desc<T>& d, int y0, type
     using C = typename CT<T>::t;
     constexpr int M = Cfg::M, SP = Cfg::SP, ROWS = Cfg::ROWS, NT = Cfg::NT;
     fft_smem<T, M, Cfg::NSEQ, SP, NT, false, true>(buf, tws);
-    // real-to-complex post-processing: X[k] = Xe[k] + W_N^k Xo[k], k = 0..M
+    // real-to-complex post-processing of z = FFT(x[2n] + i x[2n+1]):
+    //   X[k] = e + t,  e = (z[k] + conj z[M-k]) / 2,  t = W_N^k (z[k] - conj z[M-k]) / 2i,
+    // and, from the same two values, X[M-k] = conj(e - t) (W_N^(M-k) = -conj W_N^k);
+    // k = 0 gives X[0] and X[M], and its lane also writes the self-paired X[M/2] = conj z[M/2].
+    constexpr int H = M / 2;
     const C* twN = tws + Cfg::TWF;
     const unsigned plane = (unsigned)d.ny * d.wp;   // 32-bit indices: < 2^32 elements
-    for (int t = threadIdx.x; t < Cfg::NSEQ * (M + 1); t += NT) {
-        const int s = t / (M + 1), k = t % (M + 1);
+    for (int t = threadIdx.x; t < Cfg::NSEQ * H; t += NT) {
+        const int s = t / H, k = t % H;
         const int c = s / ROWS, row = s % ROWS;
-        C zk = buf[s * SP + pidx(k == M ? 0 : k)];
+        C* out = d.S + (c * plane + (unsigned)(y0 + row) * d.wp);
+        C zk = buf[s * SP + pidx(k)];
         C zm = buf[s * SP + pidx(k == 0 ? 0 : M - k)];
         zm.y = -zm.y;
         C e = C{T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y + zm.y)};
         C o = C{T(0.5) * (zk.y - zm.y), T(-0.5) * (zk.x - zm.x)};
-        C X = cadd(e, cmul(twN[k], o));
-        d.S[c * plane + (unsigned)(y0 + row) * d.wp + k] = X;
+        C tk = cmul(twN[k], o);
+        out[k] = cadd(e, tk);
+        out[M - k] = C{e.x - tk.x, tk.y - e.y};
+        if (k == 0) {
+            C zh = buf[s * SP + pidx(H)];
+            out[H] = C{zh.x, -zh.y};
+        }
     }
 }
 
-// staged row twiddles: FFT table of length M at pidx(j), then exp(-2 pi i k / NX), k <= M
+// staged row twiddles: FFT table of length M at pidx(j), then exp(-2 pi i k / NX), k < M/2
 template <typename T, int NX, int NC>
 __device__ __forceinline__ void stage_row_twiddles(const Desc<T>& d, typename CT<T>::t* tws) {
     using Cfg = RowCfg<T, NX, NC>;
     using C = typename CT<T>::t;
     constexpr int M = Cfg::M;
-    for (int t = threadIdx.x; t < M + M + 1; t += blockDim.x)
+    for (int t = threadIdx.x; t < M + M / 2; t += blockDim.x)
         cp_async<sizeof(C)>(t < M ? &tws[pidx(t)] : &tws[Cfg::TWF + (t - M)], t < M ? &d.tw[M + t] : &d.tw[NX + (t - M)]);
 }
 
@@ -388,7 +398,9 @@ __device__ __forceinline__ void row_inv_item(const Desc<T>& d, const typename F:
     const unsigned plane = (unsigned)d.ny * d.wp;   // 32-bit indices: < 2^32 elements
     // complex-to-real pre-processing: Z[k] = A + i B,
     //   A = X[k] + conj(X[M-k]),  B = (X[k] - conj(X[M-k])) e^{+2 pi i k/N}
-    // (imaginary parts of X[0] and X[M] are dropped, as for a real inverse).
+    // (imaginary parts of X[0] and X[M] are dropped, as for a real inverse); the same two
+    // values give Z[M-k] = conj(A) + i conj(B), and Z[M/2] = 2 conj(X[M/2]) (k and M - k
+    // together, k < M/2; the k = 0 lane forms Z[0] and Z[M/2]).
     // stage the half spectrum rows in shared memory (asynchronous copies), then combine
     for (int t = threadIdx.x; t < Cfg::NSEQ * (M + 1); t += NT) {
         const int s = t / (M + 1), k = t % (M + 1);
@@ -397,25 +409,35 @@ __device__ __forceinline__ void row_inv_item(const Desc<T>& d, const typename F:
     }
     cp_async_wait_all();
     __syncthreads();
-    C z[(Cfg::NSEQ * M + NT - 1) / NT];
+    constexpr int H = M / 2, NI = (Cfg::NSEQ * H + NT - 1) / NT;
+    C z[NI][2];
 #pragma unroll
-    for (int u = 0; u < (Cfg::NSEQ * M + NT - 1) / NT; ++u) {
+    for (int u = 0; u < NI; ++u) {
         const int t = threadIdx.x + u * NT;
-        if ((Cfg::NSEQ * M) % NT == 0 || t < Cfg::NSEQ * M) {
-            const int s = t / M, k = t % M;
+        if ((Cfg::NSEQ * H) % NT == 0 || t < Cfg::NSEQ * H) {
+            const int s = t / H, k = t % H;
             C xk = buf[s * SP + pidx(k)], xm = buf[s * SP + pidx(M - k)];
             if (k == 0) { xk.y = T(0); xm.y = T(0); }
             xm.y = -xm.y;
             C A = cadd(xk, xm);
             C B = cmulc(csub(xk, xm), twN[k]);
-            z[u] = C{A.x - B.y, A.y + B.x};
+            z[u][0] = C{A.x - B.y, A.y + B.x};
+            z[u][1] = C{A.x + B.y, B.x - A.y};
+            if (k == 0) {
+                const C xh = buf[s * SP + pidx(H)];
+                z[u][1] = C{T(2) * xh.x, T(-2) * xh.y};
+            }
         }
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < (Cfg::NSEQ * M + NT - 1) / NT; ++u) {
+    for (int u = 0; u < NI; ++u) {
         const int t = threadIdx.x + u * NT;
-        if ((Cfg::NSEQ * M) % NT == 0 || t < Cfg::NSEQ * M) buf[(t / M) * SP + pidx(t % M)] = z[u];
+        if ((Cfg::NSEQ * H) % NT == 0 || t < Cfg::NSEQ * H) {
+            const int s = t / H, k = t % H;
+            buf[s * SP + pidx(k)] = z[u][0];
+            buf[s * SP + pidx(k == 0 ? H : M - k)] = z[u][1];
+        }
     }
     __syncthreads();
     fft_smem<T, M, Cfg::NSEQ, SP, NT, true, true>(buf, tws);

@@ -168,7 +168,7 @@ __device__ __noinline__ bool row_fwd_phase(const Desc<float>& d, float2* work, c
 template <class OP>
 __device__ __noinline__ bool col_phase(const Desc<float>& d, float2* work, const float2* ctw, long long spin) {
     const ModeK<float> mk(d);
-    for (int item = blockIdx.x; item < d.wp / PB_CW; item += gridDim.x) {
+    for (int item = blockIdx.x; item < (d.nx / 2 + PB_CW) / PB_CW; item += gridDim.x) {   // mode columns only
         __syncthreads();
         col512_item<float, 1, OP, PB_CW>(d, mk, item * PB_CW, work, ctw);
     }

@@ -293,8 +293,9 @@ void go_row_inv(const Desc<T>* d, int np, int ny, cudaStream_t st, int key) {
     if (tm) timing_end(key, st);
     count_launch();
 }
+// nm = nx/2 + 1 mode columns: ceil(nm / columns per block) blocks per problem
 template <typename T, int NY, int NC, class OP>
-void go_col(const Desc<T>* d, int np, int wp, cudaStream_t st, int key) {
+void go_col(const Desc<T>* d, int np, int nm, cudaStream_t st, int key) {
     const bool tm = timing_on();
     if (tm) timing_begin(key, st);
     if constexpr (NY == 512 && sizeof(T) == 4) {   // register-resident radix-8 stages (FP64: too many registers)
@@ -302,18 +303,18 @@ void go_col(const Desc<T>* d, int np, int wp, cudaStream_t st, int key) {
             using Cfg = Col512Cfg<T, NC, 2>;
             auto fn = k_col512<T, NC, OP, 2>;
             smem_optin((const void*)fn, Cfg::SMEM);
-            launch_pdl<T>(fn, dim3(wp / 2, np), dim3(Cfg::NT), Cfg::SMEM, st, d);
+            launch_pdl<T>(fn, dim3((nm + 1) / 2, np), dim3(Cfg::NT), Cfg::SMEM, st, d);
         } else {
             using Cfg = Col512Cfg<T, NC, COL512_CW>;
             auto fn = k_col512<T, NC, OP, COL512_CW>;
             smem_optin((const void*)fn, Cfg::SMEM);
-            launch_pdl<T>(fn, dim3(wp / COL512_CW, np), dim3(Cfg::NT), Cfg::SMEM, st, d);
+            launch_pdl<T>(fn, dim3((nm + COL512_CW - 1) / COL512_CW, np), dim3(Cfg::NT), Cfg::SMEM, st, d);
         }
     } else {
         using Cfg = ColCfg<T, NY, NC>;
         auto fn = k_col<T, NY, NC, OP>;
         smem_optin((const void*)fn, Cfg::SMEM);
-        launch_pdl<T>(fn, dim3(wp / Cfg::CWE, np), dim3(Cfg::NT), Cfg::SMEM, st, d);
+        launch_pdl<T>(fn, dim3((nm + Cfg::CWE - 1) / Cfg::CWE, np), dim3(Cfg::NT), Cfg::SMEM, st, d);
     }
     if (tm) timing_end(key, st);
     count_launch();
