@@ -194,8 +194,15 @@ struct RowCfg {
     static constexpr int NT = (NC * ROWS * M >= 1024) ? 256 : 128;
     // FP32 forward passes: ask the register allocator for 8 resident 128-thread
     // blocks per SM (64 registers), so that enough loads are in flight, on the
-    // sizes where the tangent of the mechanics pass fits without spilling
-    static constexpr int MINB = (sizeof(T) == 4 && (NX == 128 || NX == 512 || NX == 1024)) ? 8 * 128 / NT : 1;
+    // sizes where the tangent of the mechanics pass fits without spilling; the
+    // 512-point three-component pass takes 9 (56 registers, 8 bytes of spill:
+    // measured 0.7 % faster in the concurrent-stream launch mode)
+    static constexpr int MINB = (sizeof(T) == 4 && (NX == 128 || NX == 512 || NX == 1024))
+                                    ? (NX == 512 && NC == 3 ? 9 : 8) * 128 / NT : 1;
+    // FP32 512-point inverse passes: 6 resident blocks per SM (80 registers; a few bytes of
+    // spill in the update kernels), measured faster than 5 blocks at 96 registers when the
+    // one- and three-component passes of concurrent simulations share the SMs
+    static constexpr int MINB_INV = (sizeof(T) == 4 && NX == 512) ? 6 : 1;
     static constexpr int SP = padded_len(M) + 2;            // pitch (complex): padded M values + slot for k = M
     static constexpr int NSEQ = NC * ROWS;
     // twiddles staged in shared memory: length-M FFT table (padded indices) + the
@@ -466,7 +473,7 @@ __device__ __forceinline__ void row_inv_item(const Desc<T>& d, const typename F:
 }
 
 template <typename T, int NX, int NC, class F>
-__global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv(const Desc<T>* __restrict__ descs) {
+__global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB_INV) k_row_inv(const Desc<T>* __restrict__ descs) {
     using Cfg = RowCfg<T, NX, NC>;
     using C = typename CT<T>::t;
     constexpr int NT = Cfg::NT;
