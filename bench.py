@@ -719,7 +719,7 @@ def grid64_whole_run(pff, torch, stream, sp, oracle_steps=12):
     return res
 
 
-def grid2048(pff, torch, stream, sp, warm=1, steps=3):
+def grid2048(pff, torch, stream, sp, warm=2, steps=8):
     """One 2048x2048 grid, correlation length 64 px, ell = 2 px, AT2 strain-spectral, crack set,
     mixed precision, from 0.97 eps_M: load steps timed with CUDA events, then one more load step
     with per-kernel event timing for the roofline of its dominant kernel class."""
@@ -754,7 +754,7 @@ def grid2048(pff, torch, stream, sp, warm=1, steps=3):
                       f"the 300-step run); kernel classes timed over one further load step"}
 
 
-def batch64_grid256(pff, torch, stream, sp, warm=1, steps=3):
+def batch64_grid256(pff, torch, stream, sp, warm=2, steps=8):
     """64 independent 256x256 microstructures (seeds 0..63, correlation length 16 px, ell = 2 px,
     AT1 strain-spectral, crack set, mixed precision) advanced together from 0.95 eps_M, launch
     grouping chosen by pff_batch_autotune; load steps timed with CUDA events; kernel classes timed

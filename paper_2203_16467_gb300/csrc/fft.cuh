@@ -274,7 +274,10 @@ __device__ __forceinline__ void row_fwd_pixels(const Desc<T>& d, const typename 
     T* rb = reinterpret_cast<T*>(buf);
     if constexpr (HasIn<F>::value && (ROWS * NX) % NT == 0) {
         constexpr int PPT = ROWS * NX / NT;
-        constexpr int G = PPT < PFF_ROW_G ? PPT : PFF_ROW_G;   // pixels whose loads are in flight together
+        // pixels whose loads are in flight together: PFF_ROW_G, or as many as about 32
+        // registers of loaded values allow (a power of two, so that it divides PPT)
+        constexpr int WORDS = (int)((sizeof(typename F::In) + 3) / 4);
+        constexpr int G = pow2floor(cmin(PPT, cmax(PFF_ROW_G, 32 / WORDS)));
 #pragma unroll
         for (int j0 = 0; j0 < PPT; j0 += G) {
             typename F::In in[G];
