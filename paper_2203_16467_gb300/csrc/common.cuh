@@ -177,14 +177,18 @@ __device__ __forceinline__ void pixel_one(const D& d, const X& c, size_t i, A&&.
 
 struct DF { float hi, lo; };   // double-float value hi + lo (see reduce_grid)
 template <typename T> struct Acc;
+// count(x): a small integer (a pixel count); a thread's sum of counts is exact in
+// either precision (below 2^24), so it needs no compensation.
 template <> struct Acc<double> {
     double s = 0.0;
     __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ void count(double x) { s += x; }
     __device__ __forceinline__ void addp(double a, double b) { s = fma(a, b, s); }
     __device__ __forceinline__ double get() const { return s; }
 };
 template <> struct Acc<float> {
     float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void count(float x) { s += x; }
     __device__ __forceinline__ void add(float x) {
         float t = s + x;
         float z = t - s;

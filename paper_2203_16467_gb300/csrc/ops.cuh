@@ -723,7 +723,7 @@ struct FPfB1 {
     }
     __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, const In& a, Acc<T>* acc) {
         T x = a.v + c.alpha * a.p;
-        if (x < a.vc) { x = a.vc; acc[0].add(T(1)); }
+        if (x < a.vc) { x = a.vc; acc[0].count(T(1)); }
         d.th[0][i] = x;
         const bool at = (x == a.vc);
         T rn = a.R + c.alpha * a.Jp;
@@ -747,7 +747,7 @@ struct FPfB1 {
         d.flags[i] = (uint8_t)((at ? 1 : 0) | (active ? 2 : 0));
         acc[1].addp(rn, rn);
         acc[2].addp(rn, a.ro);
-        acc[3].add(active ? T(1) : T(0));
+        if (active) acc[3].count(T(1));
     }
     __device__ static void finalize(const Desc<T>& d, const double* tot) {
         Ctrl* c = d.ctrl;
@@ -785,7 +785,7 @@ struct FPfA3B {   // J p from the column pass's lap p, then the iterate of FPfB1
     __device__ static void pixel(const Desc<T>& d, const Ctx& c, size_t i, const In& a, T (&lp)[1], Acc<T>* acc) {
         const T Jp = a.a * a.p - c.kappa * lp[0];
         T x = a.v + c.alpha * a.p;
-        if (x < a.vc) { x = a.vc; acc[0].add(T(1)); }
+        if (x < a.vc) { x = a.vc; acc[0].count(T(1)); }
         d.th[0][i] = x;
         const bool at = (x == a.vc);
         T rn = a.R + c.alpha * Jp;
@@ -806,7 +806,7 @@ struct FPfA3B {   // J p from the column pass's lap p, then the iterate of FPfB1
         d.flags[i] = (uint8_t)((at ? 1 : 0) | (active ? 2 : 0));
         acc[1].addp(rn, rn);
         acc[2].addp(rn, a.ro);
-        acc[3].add(active ? T(1) : T(0));
+        if (active) acc[3].count(T(1));
         if (!active) {   // sums of the next direction (free pixels)
             const T ar = a.a * rn;
             acc[4].addp(ar, rn);
@@ -876,7 +876,7 @@ struct FPfB3 {   // explicit R = J v - b, active set {bound and R > 0}, beta, co
         d.flags[i] = (uint8_t)((at ? 1 : 0) | (active ? 2 : 0));
         acc[0].addp(rn, rn);
         acc[1].addp(rn, ro);
-        acc[2].add(active ? T(1) : T(0));
+        if (active) acc[2].count(T(1));
         if (!active) {   // sums of the next direction (free pixels; used by the three-pass iteration)
             const T ar = a * rn;
             acc[3].addp(ar, rn);
