@@ -467,7 +467,8 @@ def run_ours(args, rank, world, dev):
     line = None
     extra = {}
     if rank == 0 and not args.no_baselines:
-        extra = baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed, phi_mixed)
+        dom_key = {name: k for k, name in KERNEL_NAMES.items()}[dom]
+        extra = baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed, phi_mixed, dom_key)
     for p in probs:
         pass
     pff.destroy_batch(b)
@@ -542,7 +543,7 @@ def plain_fp64(args, pff, torch, stream, sp, tol, phi_mixed):
             "phi_rel_l2_vs_mixed_max": max(diffs) if diffs else None}, finals
 
 
-def baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed, phi_mixed=None):
+def baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed, phi_mixed=None, dom_key=(0, 1)):
     out = {}
     ours_steps = len(probs) * args.steps / elapsed
     ours_iters = (mech + bccg) * N * N / elapsed
@@ -570,7 +571,7 @@ def baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed, ph
         out["cufft_comparison"] = {"error": str(e)[:200]}
     # the dominant kernel class at 1, 2, 4 and 8 identical simulations per launch
     try:
-        out["dominant_kernel_scaling"] = kernel_scaling(pff, torch, sp)
+        out["dominant_kernel_scaling"] = kernel_scaling(pff, torch, sp, key=dom_key)
     except Exception as e:
         out["dominant_kernel_scaling"] = {"error": str(e)[:200]}
     # the two BCCG iteration structures (three / four operator passes), same start, same launches
@@ -851,12 +852,14 @@ def cufft_compare(pff, torch, stream, n=N, reps=200, warm=20):
 
 
 def kernel_scaling(pff, torch, sp, key=(0, 1), variant=("AT1", "SPECTRAL", "CRACK_SET")):
-    """Average launch duration (CUDA events) and algorithmic GB/s of one kernel class when
+    """Average launch duration (CUDA events) and algorithmic GB/s of the kernel classes when
     every launch carries k identical simulations (all active in every launch), k = 1..8:
-    separates the fixed cost of a launch from the bandwidth of its work."""
+    separates the fixed cost of a launch from the bandwidth of its work.  `rows` are those of
+    class key; `classes` holds the same figures for every class of the iteration."""
     peak, _ = hbm_peak()
-    bpp = bytes_per_px(4, N)[key]
-    rows = []
+    bccg4 = pff.get_kernel_variant(pff.VARIANT_BCCG_PASSES, N, 1) == 1
+    bpp = bytes_per_px(4, N, variant[1] == "ISOTROPIC")
+    per = {k: [] for k in KERNEL_NAMES}
     for k in (1, 2, 4, 8):
         probs, _ = make_problems(pff, sp, 0, pff.MIXED, [variant] * k)
         b = pff.create_batch(k, sum(pff.problem_bytes(N, N, pff.MIXED) for _ in probs), sp)
@@ -869,20 +872,25 @@ def kernel_scaling(pff, torch, sp, key=(0, 1), variant=("AT1", "SPECTRAL", "CRAC
         pff.timing_enable(True)
         out = pff.batch_step(b, k, 1)
         pff.timing_enable(False)
-        ms, nl = pff.timing_read(*key)
+        act_all = active_launches(out, bccg4)   # problem-launches that did work
+        for kk in KERNEL_NAMES:
+            ms, nl = pff.timing_read(*kk)
+            if not nl:
+                continue
+            act = act_all[kk]
+            gbs = act * bpp[kk] * N * N / (ms * 1e-3) / 1e9 if ms > 0 else None
+            per[kk].append({"simulations_per_launch": k, "launches": nl, "working_launches": act // k,
+                            "us_per_launch": 1e3 * ms / nl, "achieved_GBs": gbs, "frac": gbs / peak if gbs else None})
         pff.destroy_batch(b)
         for p in probs:
             p.close()
-        act = active_launches(out, pff.get_kernel_variant(pff.VARIANT_BCCG_PASSES, N, 1) == 1)[key]   # working
-        work = act // k                           # launches with all k simulations working
-        gbs = act * bpp * N * N / (ms * 1e-3) / 1e9 if ms > 0 else None
-        rows.append({"simulations_per_launch": k, "launches": nl, "working_launches": work,
-                     "us_per_launch": 1e3 * ms / nl if nl else None, "achieved_GBs": gbs,
-                     "frac": gbs / peak if gbs else None})
-    return {"kernel": KERNEL_NAMES[key], "variant": "/".join(variant), "rows": rows,
+    return {"kernel": KERNEL_NAMES[key], "variant": "/".join(variant), "rows": per[key],
+            "classes": {KERNEL_NAMES[kk]: {str(r["simulations_per_launch"]): round(r["frac"], 3) if r["frac"] else None
+                                           for r in v} for kk, v in per.items() if v},
             "note": "one load step after two warm-up steps; the identical simulations work in the same "
                     "launches; the skipped launches at the end of each 8-iteration chunk count against "
-                    "the time, as in the roofline figure"}
+                    "the time, as in the roofline figure; classes: fraction of the measured peak per class "
+                    "and simulations per launch"}
 
 
 def bccg_passes_compare(pff, torch, sp, warm=3, steps=8):
