@@ -199,7 +199,13 @@ int pff_get_params(pff_problem* h, pff_params* p);
  * irreversibility: PFF_CRACK_SET|PFF_DAMAGE (Sec. 2.1, Eq. constraint_field). */
 int pff_set_model(pff_problem* h, int fracture, int split, int irreversibility);
 /* Young's modulus field E(x) >= 0 with a positive mean, nx*ny values (zeros
- * appear in the crack of pff_init_crack with PFF_IC_MODULUS). */
+ * appear in the crack of pff_init_crack with PFF_IC_MODULUS).  A field that is
+ * negative or not finite anywhere returns PFF_ERR_INVALID_ARG and leaves the
+ * stored field unchanged.  Host arrays of FP32 problems are copied as they are
+ * into a device staging buffer of nx*ny doubles (allocated on the first host
+ * transfer, freed with the problem) and converted there; page-locked host
+ * memory makes the copy a single DMA.  Returns after the copy: the caller may
+ * reuse its buffer. */
 int pff_set_modulus_field(pff_problem* h, const double* E, int on_device);
 /* Phase field, nx*ny values in [0, 1] (initial condition; default 0). */
 int pff_set_phase_field(pff_problem* h, const double* phi, int on_device);
@@ -272,7 +278,9 @@ int pff_step_load(pff_problem* h, int n_steps, pff_step_report* out, int* steps_
 int pff_solve_mechanics(pff_problem* h, pff_step_report* out);
 int pff_solve_phase_field(pff_problem* h, pff_step_report* out);
 
-/* Copy a field out (FP64, host).  Tensor fields fill 3*nx*ny values. */
+/* Copy a field out (FP64, host; FP32 problems convert on the device, through
+ * the staging buffer above).  Tensor fields fill 3*nx*ny values.  Returns when
+ * host_out holds the values. */
 int pff_get_fields(pff_problem* h, int which, double* host_out);
 /* Device view of a stored field: *p receives the device pointer, *dtype 0 for
  * FP64 / 1 for FP32; tensor fields are 3 contiguous planes.  Only fields that

@@ -270,6 +270,7 @@ struct pff_problem {
     void* field[NFIELDS] = {};
     uint8_t* flags = nullptr;
     void* S = nullptr;
+    double* stage = nullptr;       // FP64 staging for host transfers of FP32 fields (n values, on first use)
     double* part = nullptr;
     Ctrl* ctrl = nullptr;
     Twiddles tw;
@@ -379,7 +380,21 @@ static int upload_desc(pff_problem* h) {
     return e == cudaSuccess ? 0 : cuda_fail(h, e, "upload descriptor");
 }
 
-// Copy nx*ny*ncomp FP64 values (host or device) into a field of the problem's precision.
+// Device staging buffer (n doubles) through which host transfers of an FP32 problem's fields
+// pass: the FP64 host values are copied as they are and converted on the device (and back),
+// so a transfer is one DMA of the caller's buffer (fast when it is pinned) and one kernel,
+// with no conversion loop on the host.  Allocated on first use; false when it cannot be.
+static bool ensure_stage(pff_problem* h) {
+    if (h->stage) return true;
+    if (cudaMalloc(&h->stage, h->n() * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        h->stage = nullptr;
+        return false;
+    }
+    return true;
+}
+
+// Copy nx*ny FP64 values (host or device) into a field of the problem's precision.
 static int put_field(pff_problem* h, void* dst, const double* src, size_t count, int on_device) {
     cudaError_t e = cudaSuccess;
     if (h->prec == PFF_FP64) {
@@ -387,13 +402,19 @@ static int put_field(pff_problem* h, void* dst, const double* src, size_t count,
     } else if (on_device) {
         launch_convert_d2f((float*)dst, src, count, h->st);
         e = cudaGetLastError();
-    } else {
+    } else if (count <= h->n() && ensure_stage(h)) {
+        e = cudaMemcpyAsync(h->stage, src, count * 8, cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess) {
+            launch_convert_d2f((float*)dst, h->stage, count, h->st);
+            e = cudaGetLastError();
+        }
+    } else {   // no room for the staging buffer: convert on the host
         std::vector<float> tmp(count);
         for (size_t i = 0; i < count; ++i) tmp[i] = (float)src[i];
         e = cudaMemcpyAsync(dst, tmp.data(), count * 4, cudaMemcpyHostToDevice, h->st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);   // the caller may reuse its buffer on return
     return e == cudaSuccess ? 0 : cuda_fail(h, e, "copy in");
 }
 
@@ -401,6 +422,11 @@ static int get_field(pff_problem* h, const void* src, double* dst, size_t count)
     cudaError_t e;
     if (h->prec == PFF_FP64) {
         e = cudaMemcpyAsync(dst, src, count * 8, cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    } else if (count <= h->n() && ensure_stage(h)) {
+        launch_convert_f2d(h->stage, (const float*)src, count, h->st);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, h->stage, count * 8, cudaMemcpyDeviceToHost, h->st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     } else {
         std::vector<float> tmp(count);
@@ -1147,6 +1173,7 @@ int pff_destroy_problem(pff_problem* h) {
     if (h->st) cudaStreamSynchronize(h->st);
     else cudaDeviceSynchronize();
     if (h->base) cudaFree(h->base);
+    if (h->stage) cudaFree(h->stage);
     if (h->d_desc) cudaFree(h->d_desc);
     if (h->d_flags) cudaFree(h->d_flags);
     if (h->d_ctrlcopy) cudaFree(h->d_ctrlcopy);
@@ -1217,13 +1244,16 @@ int pff_set_modulus_field(pff_problem* h, const double* E, int on_device) {
     if (!(s > 0.0)) return fail(h, PFF_ERR_INVALID_ARG, "E must have a positive mean");
     int rc = put_field(h, h->field[0], E, n, on_device);
     if (rc) return rc;
+    if (s == h->sumE && s2 == h->sumE2) return PFF_OK;   // the same sums: control block and constants unchanged
     h->sumE = s;
     h->sumE2 = s2;
-    if ((rc = read_ctrl(h))) return rc;
-    h->h_ctrl->sumE = s;
+    // the two sums only (adjacent in the control block), from the pinned host mirror
+    static_assert(offsetof(Ctrl, sumE) == offsetof(Ctrl, sumE2) + sizeof(double), "sumE2, sumE adjacent");
     h->h_ctrl->sumE2 = s2;
-    if ((rc = write_ctrl(h))) return rc;
-    return upload_desc(h);
+    h->h_ctrl->sumE = s;
+    cudaError_t e = cudaMemcpyAsync(&h->ctrl->sumE2, &h->h_ctrl->sumE2, 2 * sizeof(double), cudaMemcpyHostToDevice, h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "write modulus sums");
+    return upload_desc(h);   // C_broken follows the mean modulus; synchronises the stream
 }
 
 int pff_init_crack(pff_problem* h, int target, int shape, double xc, double yc, double length, double E0) {

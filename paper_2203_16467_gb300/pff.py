@@ -330,10 +330,15 @@ def solve_phase_field(h):
     return r.to_dict()
 
 
-def get_fields(h, which):
+def get_fields(h, which, out=None):
+    """FP64 copy of a field; out: a C-contiguous float64 array of the field's size to fill
+    (for example one backed by pinned memory), else a new array."""
     nx, ny, _ = _nxny(h)
     ncomp = 3 if which in _TENSOR_FIELDS else 1
-    out = np.empty(ncomp * nx * ny, dtype=np.float64)
+    if out is None:
+        out = np.empty(ncomp * nx * ny, dtype=np.float64)
+    elif out.dtype != np.float64 or out.size != ncomp * nx * ny or not out.flags.c_contiguous:
+        raise ValueError(f"out must be a C-contiguous float64 array of {ncomp * nx * ny} values")
     _check(lib.pff_get_fields(h, which, _dptr(out)), h)
     return out.reshape((3, ny, nx) if ncomp == 3 else (ny, nx))
 

@@ -93,3 +93,38 @@ def test_constitutive_parity(pff, prec, split):
     # special points above probe: there both sides take the ramp derivative at e1
     assert tensor_rel_l2(tang, tref) < (1e-11 if prec == 0 else 2e-6)
     p.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_host_field_transfers(pff, prec):
+    # fields in and out through host buffers (FP32 problems convert on the device through a
+    # staging buffer): FP64 values come back exactly, FP32 ones as the FP32 rounding of the input,
+    # into new arrays and into caller-provided (pinned) ones
+    import torch
+    nx, ny = 128, 64
+    rng = np.random.default_rng(5)
+    E = np.exp(0.3 * rng.standard_normal((ny, nx)))
+    phi = rng.uniform(0.0, 0.9, (ny, nx))
+    eps = 1e-3 * rng.standard_normal((3, ny, nx))
+    rnd = (lambda a: a) if prec == 0 else (lambda a: a.astype(np.float32).astype(np.float64))
+    p = pff.Problem(nx, ny, prec, E=E)
+    p.set_phase_field(phi)
+    p.set_strain(eps.reshape(3, -1), (0.0, 0.0, 0.0))
+    assert np.array_equal(p.get_fields(pff.FIELD_MODULUS), rnd(E))
+    assert np.array_equal(p.get_fields(pff.FIELD_PHI), rnd(phi))
+    assert np.array_equal(p.get_fields(pff.FIELD_EPS_STAR), rnd(eps))
+    pin = torch.empty(nx * ny, dtype=torch.float64, pin_memory=True)
+    pin_np = pin.numpy()
+    pin_np[:] = (2.0 * E).ravel()
+    p.set_modulus_field(pin_np)
+    out = torch.empty(nx * ny, dtype=torch.float64, pin_memory=True).numpy()
+    got = p.get_fields(pff.FIELD_MODULUS, out=out)
+    assert np.shares_memory(got, out) and np.array_equal(got, rnd(2.0 * E))
+    p.set_modulus_field(2.0 * E)          # the same values again (sums unchanged)
+    assert np.array_equal(p.get_fields(pff.FIELD_MODULUS), rnd(2.0 * E))
+    with pytest.raises(ValueError):
+        p.get_fields(pff.FIELD_PHI, out=np.empty(nx * ny - 1))
+    with pytest.raises(pff.PffError):
+        p.set_modulus_field(-E)           # rejected on the host, the stored field unchanged
+    assert np.array_equal(p.get_fields(pff.FIELD_MODULUS), rnd(2.0 * E))
+    p.close()
