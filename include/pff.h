@@ -202,10 +202,9 @@ int pff_set_model(pff_problem* h, int fracture, int split, int irreversibility);
  * appear in the crack of pff_init_crack with PFF_IC_MODULUS).  A field that is
  * negative or not finite anywhere returns PFF_ERR_INVALID_ARG and leaves the
  * stored field unchanged.  Host arrays of FP32 problems are copied as they are
- * into a device staging buffer of nx*ny doubles (allocated on the first host
- * transfer, freed with the problem) and converted there; page-locked host
- * memory makes the copy a single DMA.  Returns after the copy: the caller may
- * reuse its buffer. */
+ * into a device staging buffer of nx*ny doubles (part of the problem, counted
+ * by pff_problem_bytes) and converted there; page-locked host memory makes the
+ * copy a single DMA.  Returns after the copy: the caller may reuse its buffer. */
 int pff_set_modulus_field(pff_problem* h, const double* E, int on_device);
 /* Phase field, nx*ny values in [0, 1] (initial condition; default 0). */
 int pff_set_phase_field(pff_problem* h, const double* phi, int on_device);

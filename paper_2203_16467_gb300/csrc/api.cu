@@ -228,6 +228,7 @@ static size_t problem_bytes(int nx, int ny, int prec) {
     b += align256(n);                                              // flags
     b += align256((size_t)3 * ny * wp_of(nx) * 2 * es);            // spectrum
     b += align256((size_t)PART_BLOCKS * 8 * sizeof(double));       // partials
+    if (prec != PFF_FP64) b += align256(n * sizeof(double));       // FP64 staging of host transfers
     b += align256(sizeof(Ctrl));
     return b;
 }
@@ -270,7 +271,7 @@ struct pff_problem {
     void* field[NFIELDS] = {};
     uint8_t* flags = nullptr;
     void* S = nullptr;
-    double* stage = nullptr;       // FP64 staging for host transfers of FP32 fields (n values, on first use)
+    double* stage = nullptr;       // FP64 staging for host transfers of FP32 fields (n values; FP32 problems)
     double* part = nullptr;
     Ctrl* ctrl = nullptr;
     Twiddles tw;
@@ -380,19 +381,11 @@ static int upload_desc(pff_problem* h) {
     return e == cudaSuccess ? 0 : cuda_fail(h, e, "upload descriptor");
 }
 
-// Device staging buffer (n doubles) through which host transfers of an FP32 problem's fields
-// pass: the FP64 host values are copied as they are and converted on the device (and back),
-// so a transfer is one DMA of the caller's buffer (fast when it is pinned) and one kernel,
-// with no conversion loop on the host.  Allocated on first use; false when it cannot be.
-static bool ensure_stage(pff_problem* h) {
-    if (h->stage) return true;
-    if (cudaMalloc(&h->stage, h->n() * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        h->stage = nullptr;
-        return false;
-    }
-    return true;
-}
+// FP32 problems hold a staging buffer of n doubles (part of the problem's allocation) through
+// which host transfers of their fields pass: the FP64 host values are copied as they are and
+// converted on the device (and back), so a transfer is one DMA of the caller's buffer (fast
+// when it is page-locked) and one kernel, with no conversion loop on the host.
+static bool ensure_stage(pff_problem* h) { return h->stage != nullptr; }
 
 // Copy nx*ny FP64 values (host or device) into a field of the problem's precision.
 static int put_field(pff_problem* h, void* dst, const double* src, size_t count, int on_device) {
@@ -1149,6 +1142,7 @@ int pff_create_problem(int nx, int ny, int precision, void* cuda_stream, pff_pro
     h->flags = (uint8_t*)p; p += align256(n);
     h->S = p; p += align256((size_t)3 * ny * h->wp * 2 * es);
     h->part = (double*)p; p += align256((size_t)PART_BLOCKS * 8 * sizeof(double));
+    if (precision != PFF_FP64) { h->stage = (double*)p; p += align256(n * sizeof(double)); }
     h->ctrl = (Ctrl*)p;
     e = cudaMemsetAsync(h->base, 0, h->bytes, h->st);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_desc, sizeof(Desc<double>));
@@ -1173,7 +1167,6 @@ int pff_destroy_problem(pff_problem* h) {
     if (h->st) cudaStreamSynchronize(h->st);
     else cudaDeviceSynchronize();
     if (h->base) cudaFree(h->base);
-    if (h->stage) cudaFree(h->stage);
     if (h->d_desc) cudaFree(h->d_desc);
     if (h->d_flags) cudaFree(h->d_flags);
     if (h->d_ctrlcopy) cudaFree(h->d_ctrlcopy);
