@@ -354,7 +354,7 @@ __device__ __forceinline__ void stage_row_twiddles(const Desc<T>& d, typename CT
 }
 
 template <typename T, int NX, int NC, class F>
-__global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB) k_row_fwd(const Desc<T>* __restrict__ descs) {
+__device__ __forceinline__ void row_fwd_body(const Desc<T>* __restrict__ descs) {
     using Cfg = RowCfg<T, NX, NC>;
     using C = typename CT<T>::t;
     constexpr int NT = Cfg::NT;
@@ -380,6 +380,19 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB
     cp_async_wait_all();
     __syncthreads();
     row_fwd_fft_store<T, NX, NC>(d, y0, buf, tws);
+}
+
+// Each row kernel comes in two forms: with the register cap of its configuration (minimum
+// resident blocks per SM; the FP32 sizes whose caps were chosen by measurement) and, suffix
+// _u, without a minimum (the compiler's own choice: a minimum of one block is not the same as
+// no bound to ptxas, which then takes more registers).
+template <typename T, int NX, int NC, class F>
+__global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB) k_row_fwd(const Desc<T>* __restrict__ descs) {
+    row_fwd_body<T, NX, NC, F>(descs);
+}
+template <typename T, int NX, int NC, class F>
+__global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_fwd_u(const Desc<T>* __restrict__ descs) {
+    row_fwd_body<T, NX, NC, F>(descs);
 }
 
 // Row-inverse pass of one row group y0: the epilogue's pixel loads are issued
@@ -476,7 +489,7 @@ __device__ __forceinline__ void row_inv_item(const Desc<T>& d, const typename F:
 }
 
 template <typename T, int NX, int NC, class F>
-__global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB_INV) k_row_inv(const Desc<T>* __restrict__ descs) {
+__device__ __forceinline__ void row_inv_body(const Desc<T>* __restrict__ descs) {
     using Cfg = RowCfg<T, NX, NC>;
     using C = typename CT<T>::t;
     constexpr int NT = Cfg::NT;
@@ -496,6 +509,14 @@ __global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB
         if (reduce_acc<F::NR, NT>(acc, d.part, &d.ctrl->counter, gridDim.x, tot) && threadIdx.x == 0)
             F::finalize(d, tot);
     }
+}
+template <typename T, int NX, int NC, class F>
+__global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT, RowCfg<T, NX, NC>::MINB_INV) k_row_inv(const Desc<T>* __restrict__ descs) {
+    row_inv_body<T, NX, NC, F>(descs);
+}
+template <typename T, int NX, int NC, class F>
+__global__ void __launch_bounds__(RowCfg<T, NX, NC>::NT) k_row_inv_u(const Desc<T>* __restrict__ descs) {
+    row_inv_body<T, NX, NC, F>(descs);
 }
 
 // Column pass: CWE adjacent columns kx of the half spectrum, all NC planes.

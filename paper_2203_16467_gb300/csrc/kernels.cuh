@@ -274,7 +274,9 @@ enum { FAM_ROW_FWD = 0, FAM_ROW_INV = 1, FAM_COL = 2, FAM_ELEM = 3, FAM_CLUSTER 
 template <typename T, int NX, int NC, class F>
 void go_row_fwd(const Desc<T>* d, int np, int ny, cudaStream_t st, int key) {
     using Cfg = RowCfg<T, NX, NC>;
-    auto fn = k_row_fwd<T, NX, NC, F>;
+    void (*fn)(const Desc<T>*);
+    if constexpr (Cfg::MINB > 1) fn = k_row_fwd<T, NX, NC, F>;
+    else fn = k_row_fwd_u<T, NX, NC, F>;
     smem_optin((const void*)fn, Cfg::SMEM);
     const bool tm = timing_on();
     if (tm) timing_begin(key, st);
@@ -285,7 +287,9 @@ void go_row_fwd(const Desc<T>* d, int np, int ny, cudaStream_t st, int key) {
 template <typename T, int NX, int NC, class F>
 void go_row_inv(const Desc<T>* d, int np, int ny, cudaStream_t st, int key) {
     using Cfg = RowCfg<T, NX, NC>;
-    auto fn = k_row_inv<T, NX, NC, F>;
+    void (*fn)(const Desc<T>*);
+    if constexpr (Cfg::MINB_INV > 1) fn = k_row_inv<T, NX, NC, F>;
+    else fn = k_row_inv_u<T, NX, NC, F>;
     smem_optin((const void*)fn, Cfg::SMEM);
     const bool tm = timing_on();
     if (tm) timing_begin(key, st);
