@@ -593,21 +593,24 @@ def baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed, ph
     E_pin = pin_t[0].numpy()
     E_pin[:] = np.asarray(E, dtype=np.float64).ravel()
     phi_pin = [t.numpy() for t in pin_t[1:]]
+    # the simulations' transfers run from one host thread each, as a front end serving them would
+    # issue them (handles are independent; ctypes releases the GIL during each call)
+    from concurrent.futures import ThreadPoolExecutor
+    pool = ThreadPoolExecutor(max_workers=len(probs))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     it_e = 0
     for s in range(ke):
-        for p in probs:
-            p.set_modulus_field(E_pin)
+        list(pool.map(lambda p: p.set_modulus_field(E_pin), probs))
         out_s = pff.batch_step(b, len(probs), 1)
         it_e += sum(r["mech_cg_iters"] + r["bccg_iters"] for rr in out_s for r in rr)
-        for p, ph in zip(probs, phi_pin):
-            p.get_fields(pff.FIELD_PHI, out=ph)
+        list(pool.map(lambda a: a[0].get_fields(pff.FIELD_PHI, out=a[1]), zip(probs, phi_pin)))
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
+    pool.shutdown()
     out["e2e"] = {"value": it_e * N * N / te, "unit": "pixel-CG-iters/s",
                   "h2d_bytes_per_step": len(probs) * N * N * 8, "d2h_bytes_per_step": len(probs) * N * N * 8,
-                  "steps": ke, "host_buffers": "pinned (torch pin_memory), FP64",
+                  "steps": ke, "host_buffers": "pinned (torch pin_memory), FP64; one host thread per simulation",
                   "path": "pff_set_modulus_field (host E) + pff_batch_step + pff_get_fields(PHI)"}
     # the other workloads: 64x64 whole run, one 2048x2048 grid, a batch of 64 256x256 grids
     for key, fn in (("grid64_whole_run", grid64_whole_run), ("grid2048", grid2048),

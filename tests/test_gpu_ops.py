@@ -128,3 +128,29 @@ def test_host_field_transfers(pff, prec):
         p.set_modulus_field(-E)           # rejected on the host, the stored field unchanged
     assert np.array_equal(p.get_fields(pff.FIELD_MODULUS), rnd(2.0 * E))
     p.close()
+
+
+def test_host_transfers_from_concurrent_threads(pff):
+    # handles are independent: eight FP32 problems on their own streams take fields in and out
+    # from eight host threads at once (each through its own staging buffer)
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    n = 256
+    rng = np.random.default_rng(11)
+    fields = [np.exp(0.3 * rng.standard_normal((n, n))) for _ in range(8)]
+    streams = [torch.cuda.Stream() for _ in range(8)]
+    probs = [pff.Problem(n, n, pff.MIXED, stream=st.cuda_stream) for st in streams]
+
+    def roundtrip(j):
+        out = np.empty(n * n)
+        for rep in range(4):
+            probs[j].set_modulus_field(fields[j] * (rep + 1))
+            probs[j].get_fields(pff.FIELD_MODULUS, out=out)
+            if not np.array_equal(out.reshape(n, n), (fields[j] * (rep + 1)).astype(np.float32).astype(np.float64)):
+                return False
+        return True
+
+    with ThreadPoolExecutor(max_workers=8) as ex:
+        assert all(ex.map(roundtrip, range(8)))
+    for p in probs:
+        p.close()
