@@ -43,6 +43,7 @@ PRELOAD = 0.95
 VARIANTS = [(f, s, i) for f in ("AT1", "AT2") for s in ("ISOTROPIC", "SPECTRAL") for i in ("CRACK_SET", "DAMAGE")]
 WORKLOAD = "grid512_lc32_ell4_8variants_batched_mixed"
 GROUP_SIZE = 1
+FP64_RUN = False      # --precision fp64: the same batched workload with FP64 fields (not the headline)
 # Mechanics share of the iterations of the timed region (mechanics CG / (mechanics CG + BCCG)),
 # as the GPU path measures it on this workload (the "iteration_mix" key of every run reports
 # the current figure); the reference arm weights the oracle's per-iteration costs by it.
@@ -57,7 +58,8 @@ MIXED_MECH_TOL_FLOOR = 1e-6   # the library's floor on the FP32 mechanics tolera
 
 def workload_config(world=1):
     """The config dict both arms print (the workload and its effective stopping rules)."""
-    return {"workload": WORKLOAD, "grid": N, "simulations_per_gpu": len(VARIANTS),
+    return {"workload": WORKLOAD.replace("_mixed", "_fp64") if FP64_RUN else WORKLOAD, "grid": N,
+            "simulations_per_gpu": len(VARIANTS),
             "variants": ["/".join(v) for v in VARIANTS], "ell_px": ELL, "lc_px": LC, "nu": NU,
             "tol": TOL,
             "effective_tolerances": {
@@ -66,7 +68,8 @@ def workload_config(world=1):
                 "phase_field": f"BCCG ||r|| <= tol ||r0|| on explicit residuals, or in FP32 the rounding-level stop "
                                f"(64 iterations without a new smallest explicit residual, or a confirming "
                                f"evaluation that improves less than 2x)"},
-            "start": f"eps_bar_yy = {PRELOAD} eps_M", "precision": "FP32 fields, FP64 reductions",
+            "start": f"eps_bar_yy = {PRELOAD} eps_M",
+            "precision": "FP64 fields and reductions" if FP64_RUN else "FP32 fields, FP64 reductions",
             "launch_groups": (f"{len(VARIANTS) // GROUP_SIZE} concurrent streams of {GROUP_SIZE} simulation(s)"
                               if GROUP_SIZE else "one launch group on one stream"),
             "l2": "inputs larger than L2: device working set "
@@ -374,7 +377,8 @@ def run_ours(args, rank, world, dev):
     # kernel-variant autotuning on a throwaway batch of the same eight simulations from the same
     # start, launched as the timed region launches them (the choice stays set for the run)
     shape = None
-    if not args.no_tune:
+    prec, es = (pff.FP64, 8) if FP64_RUN else (pff.MIXED, 4)
+    if not args.no_tune and not FP64_RUN:
         tprobs, _ = make_problems(pff, sp, rank, pff.MIXED, VARIANTS)
         tb = pff.create_batch(len(tprobs), sum(pff.problem_bytes(N, N, pff.MIXED) for _ in tprobs), sp)
         pff.batch_set_group_size(tb, GROUP_SIZE)
@@ -392,9 +396,9 @@ def run_ours(args, rank, world, dev):
                  "how": "pff_batch_autotune_kernels: 4 rounds (alternate rounds in reverse order), in each "
                         "every one of the 8 variant combinations runs 2 load steps (1 timed) of a separate batch "
                         "of the eight simulations from the benchmark start, same launch mode"}
-    probs, E = make_problems(pff, sp, rank, pff.MIXED, VARIANTS)
+    probs, E = make_problems(pff, sp, rank, prec, VARIANTS)
     nprob = len(probs)
-    budget = sum(pff.problem_bytes(N, N, pff.MIXED) for _ in probs)
+    budget = sum(pff.problem_bytes(N, N, prec) for _ in probs)
     b = pff.create_batch(nprob, budget, sp)
     # each simulation on its own stream and host thread: the variants converge at
     # different iteration counts, and independent progress beats lock-step launches
@@ -445,7 +449,7 @@ def run_ours(args, rank, world, dev):
     # kernel-class timing (live, CUDA events on the batch stream)
     bccg4 = pff.get_kernel_variant(pff.VARIANT_BCCG_PASSES, N, 1) == 1
     kt = {k: pff.timing_read(*k) for k in KERNEL_NAMES}
-    kb = kernel_bytes(reps_k, [v[1] == "ISOTROPIC" for v in VARIANTS], 4, N, N, bccg4)
+    kb = kernel_bytes(reps_k, [v[1] == "ISOTROPIC" for v in VARIANTS], es, N, N, bccg4)
     kernels = {}
     for k, name in KERNEL_NAMES.items():
         ms, nl = kt[k]
@@ -459,14 +463,14 @@ def run_ours(args, rank, world, dev):
     dom = max(kernels, key=lambda n: kernels[n]["ms"])
     # the whole path in the timed launch mode: algorithmic bytes of every kernel class over the
     # timed region (iteration counts of its own reports) per unit of its wall time
-    timed_bytes = sum(kernel_bytes(reps, [v[1] == "ISOTROPIC" for v in VARIANTS], 4, N, N, bccg4).values())
+    timed_bytes = sum(kernel_bytes(reps, [v[1] == "ISOTROPIC" for v in VARIANTS], es, N, N, bccg4).values())
     # distributed aggregation: max time, summed work (no data-path collective)
     elapsed_max, (mech_all, bccg_all, steps_all) = aggregate(elapsed, [mech, bccg, nsteps_done], world,
                                                              f"cuda:{dev}")
     value = (mech_all + bccg_all) * N * N / elapsed_max
     line = None
     extra = {}
-    if rank == 0 and not args.no_baselines:
+    if rank == 0 and not args.no_baselines and not FP64_RUN:
         dom_key = {name: k for k, name in KERNEL_NAMES.items()}[dom]
         extra = baselines(args, pff, torch, stream, sp, probs, b, E, mech, bccg, elapsed, phi_mixed, dom_key)
     for p in probs:
@@ -475,11 +479,12 @@ def run_ours(args, rank, world, dev):
     if rank == 0:
         peak, peak_kind = hbm_peak()
         ach = kernels[dom]["achieved_GBs"]
-        ws = sum(pff.problem_bytes(N, N, pff.MIXED) for _ in probs)
+        ws = sum(pff.problem_bytes(N, N, prec) for _ in probs)
         line = {
             "metric": "pixel_cg_iters_per_s", "value": value, "unit": "pixel-CG-iters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if FP64_RUN else "f32",
+            "data": "synthetic",
             "config": workload_config(world),
             "kernel_autotune": shape,
             "iteration_mix": {"mechanics_cg": mech, "bccg": bccg,
@@ -495,7 +500,8 @@ def run_ours(args, rank, world, dev):
                          "frac": (ach / peak) if ach else None, "peak_kind": peak_kind,
                          "frac_of_nominal": (ach / NOMINAL_HBM_GBS) if ach else None,
                          "nominal_peak": NOMINAL_HBM_GBS,
-                         "traffic": measured_traffic(dom, kernels.get(dom, {}).get("alg_bytes_per_launch")),
+                         "traffic": (None if FP64_RUN else   # the committed capture is of the FP32 kernels
+                                     measured_traffic(dom, kernels.get(dom, {}).get("alg_bytes_per_launch"))),
                          "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled to this run's average launch)",
                          "timed_region": {"achieved": timed_bytes / elapsed / 1e9, "frac": timed_bytes / elapsed / 1e9 / peak,
                                           "unit": "GB/s", "what": "algorithmic bytes of all kernel classes over the "
@@ -997,12 +1003,15 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-baselines", action="store_true", help="skip the FP64 / e2e / CPU extras")
     ap.add_argument("--no-tune", action="store_true", help="keep the default kernel variants (no autotuning)")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed",
+                    help="fields in FP32 with FP64 reductions (the headline), or the same workload all in FP64")
     ap.add_argument("--group-size", type=int, default=None,
                     help="simulations per launch group (default 1: one stream per simulation; 0: all in one group)")
     args = ap.parse_args()
-    global GROUP_SIZE
+    global GROUP_SIZE, FP64_RUN
     if args.group_size is not None:
         GROUP_SIZE = args.group_size
+    FP64_RUN = args.precision == "fp64"
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
