@@ -199,10 +199,11 @@ struct RowCfg {
     // measured 0.7 % faster in the concurrent-stream launch mode)
     static constexpr int MINB = (sizeof(T) == 4 && (NX == 128 || NX == 512 || NX == 1024))
                                     ? (NX == 512 && NC == 3 ? 9 : 8) * 128 / NT : 1;
-    // FP32 512-point inverse passes: 6 resident blocks per SM (80 registers; a few bytes of
-    // spill in the update kernels), measured faster than 5 blocks at 96 registers when the
-    // one- and three-component passes of concurrent simulations share the SMs
-    static constexpr int MINB_INV = (sizeof(T) == 4 && NX == 512) ? 6 : 1;
+    // FP32 512-point inverse passes: 7 resident blocks per SM (72 registers; 16-40 bytes of
+    // spill in the update kernels), measured faster than 6 blocks at 80 registers and 5 at 96
+    // when the one- and three-component passes of concurrent simulations share the SMs (8 at 64
+    // registers spills 72 bytes and was slower)
+    static constexpr int MINB_INV = (sizeof(T) == 4 && NX == 512) ? 7 : 1;
     static constexpr int SP = padded_len(M) + 2;            // pitch (complex): padded M values + slot for k = M
     static constexpr int NSEQ = NC * ROWS;
     // twiddles staged in shared memory: length-M FFT table (padded indices) + the
