@@ -903,7 +903,7 @@ def kernel_scaling(pff, torch, sp, key=(0, 1), variant=("AT1", "SPECTRAL", "CRAC
             "classes": {KERNEL_NAMES[kk]: {str(r["simulations_per_launch"]): round(r["frac"], 3) if r["frac"] else None
                                            for r in v} for kk, v in per.items() if v},
             "note": "one load step after two warm-up steps; the identical simulations work in the same "
-                    "launches; the skipped launches at the end of each 8-iteration chunk count against "
+                    "launches; the skipped launches at the end of each 12-iteration chunk count against "
                     "the time, as in the roofline figure; classes: fraction of the measured peak per class "
                     "and simulations per launch"}
 

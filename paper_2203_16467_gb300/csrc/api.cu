@@ -455,7 +455,7 @@ struct Group {
     int precond = 0;       // BCCG with the Fourier Helmholtz preconditioner (same for all problems)
 };
 
-static const int CHUNK = 8;
+static const int CHUNK = 12;
 static bool g_graphs_enabled = true;
 static bool g_cond_nodes = false;  // BCCG explicit-residual chain in conditional graph nodes
 static bool g_persist = false;     // persistent BCCG solve for single FP32 512^2 problems (opt-in)
